@@ -1,0 +1,250 @@
+/*
+ * kn.h -- C ABI of libkn: batched explicit asymptotic integration of many
+ * independent stiff reaction networks ("zones") on one NVIDIA GB300 (sm_103a).
+ *
+ * Method (Brock, Belt, Billings & Guidry, "Explicit Integration with GPU
+ * Acceleration for Large Kinetic Networks"):
+ *   Eq. (1)  dY_i/dt = F+_i - F-_i = F+_i - k_i Y_i
+ *   Eq. (3)  Y_i' = (Y_i + dt F+_i) / (1 + k_i dt)      if k_i dt >= kappa  (Sec. 3)
+ *            Y_i' = Y_i + dt (F+_i - k_i Y_i)           otherwise (forward Euler)
+ *   Sec. 4   adaptive network timestep dt inside one hydro interval
+ *   Sec. 6   per zone the host sends abundances, T, rho, the interval and a
+ *            trial dt, and gets back abundances and a final dt.
+ *
+ * Conventions for every entry point:
+ *   - Return codes only (kn_status); no exception or abort crosses the ABI.
+ *     On any code other than KN_OK, kn_last_error() describes the failure.
+ *   - Inputs are copied; the caller keeps ownership of everything it passes.
+ *   - Pointers marked "host or device" are read according to the kn_mem
+ *     argument of the call.  Device pointers must be addressable from the
+ *     current CUDA device (e.g. torch tensors' data_ptr()).
+ *   - `stream` is a cudaStream_t passed as void* (0 = legacy default stream).
+ *     Calls that enqueue GPU work are asynchronous on that stream unless the
+ *     entry point says it synchronises.
+ *   - Not thread-safe per object: one network object must not be used from
+ *     two host threads at once.  Different objects are independent.
+ */
+#ifndef KN_H
+#define KN_H
+
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef enum {
+    KN_OK = 0,
+    KN_ERR_INVALID_ARG = 1, /* bad pointer, size, value or layout */
+    KN_ERR_CUDA = 2,        /* a CUDA runtime call failed (message has the CUDA error) */
+    KN_ERR_NOMEM = 3,       /* device or host allocation failed */
+    KN_ERR_STATE = 4        /* call out of order (e.g. integrate before zones are set) */
+} kn_status;
+
+/* Per-zone outcome, written by kn_integrate_batch. */
+typedef enum {
+    KN_ZONE_OK = 0,           /* reached t_end */
+    KN_ZONE_STEP_LIMIT = 1,   /* max_steps accepted steps before t_end */
+    KN_ZONE_DT_UNDERFLOW = 2, /* dt fell below dt_min_frac * t */
+    KN_ZONE_NONFINITE = 3,    /* max_reject consecutive rejects, the last one non-finite */
+    KN_ZONE_MAX_REJECT = 4,   /* max_reject consecutive rejects */
+    KN_ZONE_INVALID = 5,      /* zone inputs failed validation on the device */
+    KN_ZONE_PENDING = 6       /* set but not yet integrated */
+} kn_zone_status;
+
+typedef enum { KN_MEM_HOST = 0, KN_MEM_DEVICE = 1 } kn_mem;
+
+typedef enum {
+    KN_PREC_FP64 = 0, /* every step of the path in FP64 */
+    KN_PREC_MIXED = 1 /* FP32 rates and fluxes, Kahan-compensated FP32 gathers,
+                         FP64 update, conservation sum and error test */
+} kn_precision;
+
+/*
+ * Network description (Sec. 2 and Sec. 6: the rate-library parameters that are
+ * copied to the GPU once and stay resident).  Reaction j has 1..3 reactant
+ * slots and 1..3 product slots; a species id repeated in a list is a repeated
+ * reactant/product (i + i -> k).  Its rate is
+ *     k_j(T9, rho) = exp(ln_k0[j]) * T9^t9_exp[j] * rho^(r_j - 1),
+ * r_j = number of reactant slots, and its flux is f_j = k_j * prod(Y of reactant slots).
+ * Limits: 1 <= n_species <= 1023, 1 <= n_reactions <= 16383, and
+ * n_reactions + (reactant slots) < 65535.
+ */
+typedef struct {
+    int32_t n_species;
+    int32_t n_reactions;
+    const double *A;       /* [n_species] mass number of each species, > 0 */
+    const int32_t *reac;   /* [n_reactions][3] reactant species ids, -1 padded (ids first) */
+    const int32_t *prod;   /* [n_reactions][3] product species ids, -1 padded */
+    const double *ln_k0;   /* [n_reactions] natural log of k0_j */
+    const double *t9_exp;  /* [n_reactions] temperature exponent n_j */
+} kn_network_desc;
+
+/*
+ * Per-zone initial conditions (Sec. 6, item 1: abundances, temperature,
+ * density, hydro interval and trial timestep).  All arrays host or device
+ * (kn_mem argument), row-major:
+ *   Y0 [n_zones][n_species]  molar abundances (mass fraction X_i = A_i Y_i)
+ *   T0, rho0  [n_zones]      T9 and density at t = 0
+ *   tau       [n_zones]      profile time scale: T9(t) = T0 exp(-t/tau),
+ *                            rho(t) = rho0 exp(-3t/tau); tau <= 0 holds T9 and
+ *                            rho constant (the operator-split setting, Sec. 4)
+ *   t_start, t_end [n_zones] the interval to integrate
+ *   dt_trial  [n_zones]      first trial dt; <= 0 means t_start
+ */
+typedef struct {
+    const double *Y0;
+    const double *T0;
+    const double *rho0;
+    const double *tau;
+    const double *t_start;
+    const double *t_end;
+    const double *dt_trial;
+} kn_zone_conditions;
+
+/*
+ * Integration options.  kn_default_opts() fills the defaults listed here.
+ * The accept test and the timestep update are the library's reading of
+ * Sec. 4 (the paper states no criterion):
+ *   accept iff |sum_i A_i (Y'_i - Y_i)| <= eps_c and
+ *              max_{i: max(Y_i,Y'_i) > y_min} |Y'_i - Y_i| / max(Y_i,Y'_i) <= eps_r
+ *   accept: t += dt; dt *= min(grow_max, safety*eps_r/rel, safety*eps_c/cons)
+ *   reject: dt *= shrink, retry from the same state
+ */
+typedef struct {
+    int32_t precision;     /* kn_precision, default KN_PREC_MIXED */
+    int32_t max_reject;    /* consecutive rejects before KN_ZONE_MAX_REJECT, default 60 */
+    double kappa;          /* asymptotic switch (Sec. 3), default 1 */
+    double eps_r;          /* default 0.05 */
+    double eps_c;          /* default 1e-6 */
+    double y_min;          /* default 1e-10 */
+    double grow_max;       /* default 1.5 */
+    double safety;         /* default 0.9 */
+    double shrink;         /* default 0.5 */
+    double dt_min_frac;    /* default 1e-30 */
+    int64_t max_steps;     /* accepted steps per zone, default 10^7 */
+    /* Tiling (0 = autotuned or built-in default): threads per CTA and
+       threads per zone group.  A CTA holds threads_per_cta/threads_per_zone
+       zone slots; threads_per_zone == threads_per_cta is CTA-per-zone. */
+    int32_t threads_per_cta;
+    int32_t threads_per_zone;
+    int32_t use_graph;     /* 1: capture the launch sequence in a CUDA graph and replay it */
+    int32_t lockstep;      /* 1: zone groups of a CTA step together (required by the
+                              learned proposal); 0: independent groups. default 0 */
+    /* Replay (validation): zone z takes exactly replay_len[z] accepted steps
+       with dt = replay_dt[replay_off[z] + s], no accept test.  Device pointers;
+       zones are numbered across the nets of the call in order. NULL = off. */
+    const double *replay_dt;
+    const int64_t *replay_off;
+    const int64_t *replay_len;
+    /* Learned dt proposal (kn_mlp handle from kn_mlp_create), NULL = off. */
+    const void *mlp;
+    int64_t reserved[8];
+} kn_opts;
+
+/* Aggregate counters of the last kn_integrate_batch on these networks. */
+typedef struct {
+    int64_t zones;          /* zones integrated */
+    int64_t zones_ok;       /* of which reached t_end (KN_ZONE_OK) */
+    int64_t steps;          /* accepted steps, summed over zones */
+    int64_t rejects;        /* rejected attempts, summed over zones */
+    int64_t proposals_used; /* accepted steps whose dt came from the learned proposal */
+} kn_batch_stats;
+
+typedef struct kn_network kn_network; /* opaque, library-owned host + device copies */
+
+/* Fill *opts with the defaults documented on kn_opts.  Never fails. */
+void kn_default_opts(kn_opts *opts);
+
+/*
+ * Validate the description, build the species<->reaction maps (the CSR
+ * gathers behind the F+ and F- sums of Sec. 10 item (2)) and upload the
+ * rate parameters to the current device, where they stay resident until
+ * kn_destroy_network (Sec. 6: "copied to the GPU and resident ... for the
+ * duration of the calculation").  *out receives the new object.
+ * Errors: KN_ERR_INVALID_ARG (NULL pointers, sizes beyond the limits, a
+ * species id out of range, a reaction with no reactant or product, a
+ * non-finite parameter, A <= 0), KN_ERR_NOMEM, KN_ERR_CUDA.
+ */
+kn_status kn_create_network(const kn_network_desc *desc, kn_network **out);
+
+/* Free all host and device memory of the network (after synchronising the
+   device).  NULL is accepted and ignored. */
+kn_status kn_destroy_network(kn_network *net);
+
+/* Sizes of a network: n_species, n_reactions, reactant slots, product slots
+   (any pointer may be NULL). */
+kn_status kn_network_info(const kn_network *net, int32_t *n_species, int32_t *n_reactions,
+                          int32_t *n_reactant_slots, int32_t *n_product_slots);
+
+/*
+ * Load n_zones zones into the network's device state (Sec. 6, step 1: the
+ * host-to-device copy of abundances, T, rho, interval and trial dt), replacing
+ * any previous zones.  Enqueued on `stream`.  Host inputs are validated on the
+ * host (finite, Y0 >= 0, T0 > 0, rho0 > 0, t_end > t_start >= 0, and
+ * t_start > 0 or dt_trial > 0) and an invalid zone fails the call with
+ * KN_ERR_INVALID_ARG; device inputs are validated by the integrator, which
+ * marks an invalid zone KN_ZONE_INVALID.  Device state is (re)allocated only
+ * when n_zones grows.
+ * Errors: KN_ERR_INVALID_ARG, KN_ERR_NOMEM, KN_ERR_CUDA.
+ */
+kn_status kn_set_zone_conditions(kn_network *net, int32_t n_zones, const kn_zone_conditions *zc,
+                                 int32_t mem, void *stream);
+
+/*
+ * Integrate every zone of every listed network from t_start to t_end
+ * (Sec. 3 update, Sec. 4 adaptive steps, Sec. 9 many networks at once),
+ * entirely on the GPU in one persistent-kernel launch fed by a work queue.
+ * Zones of networks of different sizes share the launch.  Asynchronous on
+ * `stream`: results are in the networks' device state when the stream
+ * reaches this point; read them with kn_get_abundances.  Results overwrite
+ * the zone abundances in place, so a second call continues from them once
+ * new conditions are set.  nets must be distinct.
+ * Errors: KN_ERR_INVALID_ARG (bad opts or tiling), KN_ERR_STATE (a network
+ * without zones), KN_ERR_CUDA.
+ */
+kn_status kn_integrate_batch(kn_network *const *nets, int32_t n_nets, const kn_opts *opts,
+                             void *stream);
+
+/*
+ * Copy results out (Sec. 6, step 3: abundances and the final dt, plus
+ * per-zone counters).  Synchronises `stream` first.  Any output pointer may
+ * be NULL.  Layouts: Y [n_zones][n_species]; t, dt_next [n_zones] double;
+ * steps, rejects [n_zones] int64; status [n_zones] int32 (kn_zone_status).
+ * dt_next is the controller's proposal after the last accepted step, the
+ * trial dt for the next hydro interval.
+ * Errors: KN_ERR_INVALID_ARG, KN_ERR_STATE, KN_ERR_CUDA.
+ */
+kn_status kn_get_abundances(const kn_network *net, double *Y, double *t, double *dt_next,
+                            int64_t *steps, int64_t *rejects, int32_t *status, int32_t mem,
+                            void *stream);
+
+/* Sum the per-zone counters of the listed networks into *stats.
+   Synchronises `stream`.  Errors: KN_ERR_INVALID_ARG, KN_ERR_CUDA. */
+kn_status kn_get_batch_stats(kn_network *const *nets, int32_t n_nets, void *stream,
+                             kn_batch_stats *stats);
+
+/*
+ * Diagnostic single step (Eq. 1 and Eq. 3 from one state): for every zone of
+ * `net`, evaluate the rates at (T9, rho)(t_start), the fluxes and the F+/k
+ * gathers at Y0, and apply one kappa-switched update with dt = dt_trial,
+ * without the accept test, through the same device code as the integrator.
+ * Outputs (device pointers, any may be NULL): Fp, k [n_zones][n_species]
+ * double, Y1 [n_zones][n_species] double, cons [n_zones] (|sum A dY|),
+ * rel [n_zones] (max relative change, as in the accept test).  The zone
+ * state is left as set.  Asynchronous on `stream`.
+ * Errors: KN_ERR_INVALID_ARG, KN_ERR_STATE, KN_ERR_CUDA.
+ */
+kn_status kn_probe_step(kn_network *net, const kn_opts *opts, double *Fp, double *k, double *Y1,
+                        double *cons, double *rel, void *stream);
+
+/* Human-readable description of the most recent failure on this host thread
+   (empty string if none).  The pointer stays valid until the next call on
+   the same thread. */
+const char *kn_last_error(void);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* KN_H */
