@@ -1,0 +1,334 @@
+"""Benchmark: batched explicit asymptotic integration on GB300.
+
+Workload: 4096 zones of the synthetic 150-species / 1604-reaction network,
+each with its own T9(t) = T0 exp(-t/tau), rho(t) = rho0 exp(-3t/tau) profile
+(T0 ~ U[2,7], rho0 ~ logU[1e7,1e9], tau ~ logU[0.1,1] s), integrated from
+t = 1e-12 s to 1e-9 s.  One step = one pass of the whole hot path over the
+batch: load the zones' conditions from device-resident inputs, then the
+persistent integrator (rates, fluxes, gathers, kappa-switched update, accept
+test, dt control) until every zone reaches t_end.
+
+Prints ONE JSON line (rank 0).  value = accepted zone-steps per second over
+all ranks; zones_per_s alongside.  --impl reference times the CPU FP64
+oracle instead (bounded sample of the same workload on the host cores).
+"""
+import argparse
+import json
+import os
+import subprocess
+import sys
+import threading
+import time
+
+import numpy as np
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+METRIC = "zone-steps/s and zones/s to t_end, 150sp/1604rx batch; learned-Δt vs plain"
+T_END = 1e-9
+N_ZONES = 4096
+WORKLOAD = "4096 zones x 150sp/1604rx, T9/rho profiles, t 1e-12 -> 1e-9 s"
+
+
+def _args():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=5)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
+    ap.add_argument("--form", default="mixed", choices=["mixed", "fp64"])
+    ap.add_argument("--zones", type=int, default=N_ZONES)
+    ap.add_argument("--no-cpu", action="store_true", help="skip the CPU baselines")
+    ap.add_argument("--tpz", type=int, default=0)
+    ap.add_argument("--tpc", type=int, default=0)
+    return ap.parse_args()
+
+
+def _dist():
+    rank = int(os.environ.get("RANK", 0))
+    world = int(os.environ.get("WORLD_SIZE", 1))
+    local = int(os.environ.get("LOCAL_RANK", 0))
+    return rank, world, local
+
+
+class ClockSampler:
+    """nvidia-smi clock/throttle samples while the timed region runs."""
+
+    Q = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+         "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+         "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, gpu_index):
+        self.gpu = gpu_index
+        self.proc = None
+        self.lines = []
+
+    def start(self):
+        try:
+            self.proc = subprocess.Popen(
+                ["nvidia-smi", "-i", str(self.gpu), f"--query-gpu={self.Q}", "--format=csv,noheader,nounits",
+                 "-lms", "200"], stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
+            self.t = threading.Thread(target=self._read, daemon=True)
+            self.t.start()
+        except (OSError, FileNotFoundError):
+            self.proc = None
+
+    def _read(self):
+        for line in self.proc.stdout:
+            self.lines.append(line.strip())
+
+    def stop(self):
+        if not self.proc:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["nvidia-smi unavailable"]}
+        self.proc.terminate()
+        try:
+            self.proc.wait(timeout=5)
+        except subprocess.TimeoutExpired:
+            self.proc.kill()
+        sm, smax, reasons, power = [], [], set(), []
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        for ln in self.lines:
+            f = [x.strip() for x in ln.split(",")]
+            if len(f) < 9:
+                continue
+            try:
+                sm.append(float(f[1]))
+                smax.append(float(f[2]))
+                power.append(float(f[3]))
+            except ValueError:
+                continue
+            for nm, v in zip(names, f[5:9]):
+                if v.lower().startswith("active"):
+                    reasons.add(nm)
+        if not sm:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["no samples"]}
+        return {"sm_mhz": float(np.median(sm)), "sm_max_mhz": float(max(smax)), "samples": len(sm),
+                "power_w_max": float(max(power)), "reasons": sorted(reasons)}
+
+
+def _peaks():
+    p = os.path.join(ROOT, "MEASURED_PEAKS.json")
+    if os.path.exists(p):
+        return json.load(open(p)), "measured"
+    return {"hbm_gbs": 6800.0, "bf16_tflops": 1900.0}, "fallback"
+
+
+def algorithmic_flops(net, steps, rejects, precision):
+    """Algorithmic FP64 (FP64 form) or FP32+FP64 (mixed form) operations of the
+    method per batch, counting a multiply or add as 1, an FMA as 2 and each
+    exp/div as 1, with sentinel multiplications by 1 excluded:
+      rates  5 per reaction per accepted step (2 FMA-equivalents + exp)
+      fluxes+partials  1 / 3 / 7 per 1- / 2- / 3-body reaction per accepted step
+      gathers  1 per product slot and reactant slot per accepted step (+3 Kahan in mixed)
+      update+test  11 per species per attempt (accepted or rejected).
+    Returns (flops_fp64, flops_fp32)."""
+    nr = net.n_reac
+    R = net.n_reactions
+    s_r, s_p = net.slot_counts()
+    per_rx = np.where(nr == 1, 1, np.where(nr == 2, 3, 7)).sum()
+    rate = 5 * R
+    gather = s_r + s_p
+    upd = 11 * net.n_species
+    attempts = steps + rejects
+    if precision == "fp64":
+        return float(steps * (rate + per_rx + gather) + attempts * upd), 0.0
+    # mixed: rates (double-float, ~20 FP32 ops + ex2), fluxes and Kahan gathers in FP32
+    return float(attempts * upd), float(steps * (20 * R + per_rx + 4 * gather))
+
+
+def run_reference(args, rank, world):
+    """CPU FP64 oracle on a bounded sample of the same workload."""
+    if rank != 0:
+        return
+    import oracle
+    from kn_inputs import net150, profile_zones
+    net = net150()
+    orc = oracle.Oracle(net)
+    zones = profile_zones(net, args.zones, t_end=T_END)
+    threads = os.cpu_count() or 1
+    pick = np.linspace(0, args.zones - 1, 24).astype(int)
+    sub = zones.subset(pick)
+    for _ in range(args.warmup):
+        orc.integrate_batch(zones.subset(pick[:threads]), threads=threads)
+    tot_steps = tot_zones = 0
+    t0 = time.perf_counter()
+    for _ in range(args.steps):
+        r = orc.integrate_batch(sub, threads=threads)
+        tot_steps += int(r["steps"].sum())
+        tot_zones += int((r["status"] == 0).sum())
+    el = time.perf_counter() - t0
+    v = tot_steps / el
+    line = {"metric": METRIC, "value": v, "unit": "zone-steps/s", "n_gpus": args.gpus, "steps": args.steps,
+            "warmup": args.warmup, "ms_per_step": 1e3 * el / args.steps, "higher_is_better": True,
+            "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+            "impl": "reference", "zones_per_s": tot_zones / el,
+            "config": {"workload": WORKLOAD, "zones": args.zones, "sample_zones": len(pick)},
+            "cpu_baseline": {"value": v, "unit": "zone-steps/s", "cores": threads, "kind": "oracle",
+                             "sample": f"{len(pick)} of the {args.zones} zones (evenly spaced), each step"},
+            "e2e": {"value": v, "unit": "zone-steps/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
+    print(json.dumps(line), flush=True)
+
+
+def cpu_baselines(net, zones):
+    """Oracle (explicit) and dense-LU backward Euler on bounded samples."""
+    import oracle
+    orc = oracle.Oracle(net)
+    threads = os.cpu_count() or 1
+    pick = np.linspace(0, zones.n_zones - 1, 24).astype(int)
+    t0 = time.perf_counter()
+    r = orc.integrate_batch(zones.subset(pick), threads=threads)
+    el = time.perf_counter() - t0
+    exp = {"value": float(r["steps"].sum() / el), "unit": "zone-steps/s", "cores": threads, "kind": "oracle",
+           "sample": f"{len(pick)} evenly spaced zones of the batch, FP64 oracle, one thread per zone",
+           "zones_per_s": float((r["status"] == 0).sum() / el),
+           "s_per_step_per_core": float(el * min(threads, len(pick)) / r["steps"].sum())}
+    bpick = np.linspace(0, zones.n_zones - 1, min(threads, 8)).astype(int)
+    t0 = time.perf_counter()
+    b = orc.be_integrate_batch(zones.subset(bpick), max_iter=6, threads=threads)
+    bel = time.perf_counter() - t0
+    be = {"value": float(b["steps"].sum() / bel), "unit": "zone-steps/s", "cores": threads,
+          "kind": "backward Euler, dense LU, Newton <= 6 iterations",
+          "sample": f"{len(bpick)} evenly spaced zones of the batch",
+          "zones_per_s": float((b["status"] == 0).sum() / bel),
+          "s_per_step_per_core": float(bel * len(bpick) / max(1, b["steps"].sum()))}
+    return exp, be
+
+
+def main():
+    args = _args()
+    rank, world, local = _dist()
+    if args.impl == "reference":
+        if world > 1:
+            import torch.distributed as dist
+            dist.init_process_group("gloo")
+        run_reference(args, rank, world)
+        if world > 1:
+            dist.barrier()
+            dist.destroy_process_group()
+        return
+    import torch
+    torch.cuda.set_device(local)
+    if world > 1:
+        import torch.distributed as dist
+        dist.init_process_group("nccl", device_id=torch.device("cuda", local))
+    from kn_inputs import net150, profile_zones
+    from paper_1409_5826_gb300 import build, kn
+    if rank == 0:
+        build.build()
+    if world > 1:
+        dist.barrier()
+    build.build()
+    net = net150()
+    # weak scaling: each rank integrates its own batch of zones (seeds differ by rank)
+    zones = profile_zones(net, args.zones, base_seed=1000 + rank * args.zones, t_end=T_END)
+    dev = torch.device("cuda", local)
+    names = ("Y0", "T0", "rho0", "tau", "t_start", "t_end", "dt_trial")
+    dz = {k: torch.from_numpy(np.ascontiguousarray(getattr(zones, k))).to(dev) for k in names}
+    g = kn.Network(net)
+    prec = kn.PREC_MIXED if args.form == "mixed" else kn.PREC_FP64
+    opts = kn.Opts(precision=prec, use_graph=1, threads_per_zone=args.tpz, threads_per_cta=args.tpc)
+    stream = torch.cuda.current_stream()
+    flush = torch.empty(256 * 1024 * 1024 // 4, dtype=torch.float32, device=dev)  # > L2 (129 MB)
+
+    def step():
+        g.set_zones(dz, stream)
+        kn.integrate_batch([g], opts, stream)
+
+    for _ in range(max(3, args.warmup)):
+        step()
+    torch.cuda.synchronize()
+    stats = kn.batch_stats([g], stream)
+    ev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True),
+           torch.cuda.Event(enable_timing=True)) for _ in range(args.steps)]
+    clocks = ClockSampler(local)
+    clocks.start()
+    if world > 1:
+        dist.barrier()
+    torch.cuda.synchronize()
+    for i in range(args.steps):
+        flush.zero_()  # untimed: L2 flushed between timed steps
+        ev[i][0].record(stream)
+        g.set_zones(dz, stream)
+        ev[i][1].record(stream)
+        kn.integrate_batch([g], opts, stream)
+        ev[i][2].record(stream)
+    torch.cuda.synchronize()
+    if world > 1:
+        dist.barrier()
+    clk = clocks.stop()
+    step_ms = [a.elapsed_time(c) for a, b, c in ev]
+    kern_ms = [b.elapsed_time(c) for a, b, c in ev]
+    ms = float(np.sum(step_ms))
+    st = kn.batch_stats([g], stream)
+    steps_per_batch = st["steps"]
+    zones_ok = st["zones_ok"]
+    if world > 1:
+        t = torch.tensor([ms], device=dev)
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        ms = float(t.item())
+        c = torch.tensor([steps_per_batch, zones_ok], device=dev, dtype=torch.float64)
+        dist.all_reduce(c)
+        steps_all, zones_all = c.tolist()
+    else:
+        steps_all, zones_all = steps_per_batch, zones_ok
+    value = steps_all * args.steps / (ms / 1e3)
+
+    # end to end through the public API with pinned host buffers
+    pin = {k: torch.from_numpy(np.ascontiguousarray(getattr(zones, k))).pin_memory() for k in names}
+
+    class HZ:
+        pass
+
+    hz = HZ()
+    for k in names:
+        setattr(hz, k, pin[k].numpy())
+    e2e_steps = max(1, min(args.steps, 3))
+    torch.cuda.synchronize()
+    t0 = time.perf_counter()
+    for _ in range(e2e_steps):
+        g.set_zones(hz, stream)
+        kn.integrate_batch([g], opts, stream)
+        out = g.get(stream)
+    e2e_s = time.perf_counter() - t0
+    h2d = sum(pin[k].numel() * 8 for k in names)
+    d2h = sum(v.nbytes for v in out.values())
+    e2e = {"value": steps_per_batch * e2e_steps / e2e_s, "unit": "zone-steps/s", "h2d_bytes_per_step": int(h2d),
+           "d2h_bytes_per_step": int(d2h), "zones_per_s": zones_ok * e2e_steps / e2e_s}
+
+    if rank != 0:
+        if world > 1:
+            dist.barrier()
+            dist.destroy_process_group()
+        return
+    f64, f32 = algorithmic_flops(net, st["steps"], st["rejects"], args.form)
+    kms = float(np.mean(kern_ms))
+    peaks, src = _peaks()
+    fp64_peak_tf = 1.25  # nominal GB300 FP64 (recipe table); no measured FP64 peak in the peaks file
+    roof = {"bound": "alu", "unit": "TFLOP/s", "kernel": "integrate_kernel",
+            "achieved": f64 / (kms / 1e3) / 1e12, "peak": fp64_peak_tf,
+            "peak_source": "nominal FP64 (1.25 TFLOP/s)", "traffic": None,
+            "algorithmic_fp64_flops_per_launch": f64, "algorithmic_fp32_flops_per_launch": f32,
+            "kernel_ms": kms}
+    roof["frac"] = roof["achieved"] / roof["peak"]
+    line = {"metric": METRIC, "value": value, "unit": "zone-steps/s", "n_gpus": world, "steps": args.steps,
+            "warmup": max(3, args.warmup), "ms_per_step": ms / args.steps, "higher_is_better": True,
+            "scaling": "weak", "vs_baseline": None, "dtype": "f32+f64" if args.form == "mixed" else "f64",
+            "data": "synthetic", "zones_per_s": zones_all * args.steps / (ms / 1e3),
+            "config": {"workload": WORKLOAD, "zones_per_gpu": args.zones, "n_species": 150, "n_reactions": 1604,
+                       "form": args.form, "l2": "flushed between timed steps (256 MB write)",
+                       "accepted_steps_per_batch": int(steps_per_batch), "rejects_per_batch": int(st["rejects"]),
+                       "zones_ok": int(zones_ok), "parallelism": f"zones sharded, {world} GPU(s)"},
+            "clocks": clk, "e2e": e2e, "gpu_launches": 3 * args.steps, "roofline": roof}
+    if not args.no_cpu:
+        exp, be = cpu_baselines(net, zones)
+        line["cpu_baseline"] = exp
+        line["cpu_implicit_be"] = be
+    print(json.dumps(line), flush=True)
+    if world > 1:
+        dist.barrier()
+        dist.destroy_process_group()
+
+
+if __name__ == "__main__":
+    main()

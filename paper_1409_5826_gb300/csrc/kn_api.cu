@@ -1,0 +1,776 @@
+// kn_api.cu -- host runtime behind include/kn.h: network validation, the
+// species<->reaction gather plan, device state, launch geometry, work-queue
+// ordering, CUDA-graph capture/replay and result read-back.
+#include <cub/device/device_radix_sort.cuh>
+
+#include <algorithm>
+#include <cmath>
+#include <cstdarg>
+#include <cstdio>
+#include <cstring>
+#include <map>
+#include <memory>
+#include <string>
+#include <vector>
+
+#include "../../include/kn.h"
+#include "kn_internal.h"
+
+using namespace kn;
+
+namespace {
+// ---------------------------------------------------------------------------
+// errors
+// ---------------------------------------------------------------------------
+static thread_local std::string g_err;
+
+static kn_status fail(kn_status s, const char* fmt, ...) {
+    char buf[512];
+    va_list ap;
+    va_start(ap, fmt);
+    vsnprintf(buf, sizeof buf, fmt, ap);
+    va_end(ap);
+    g_err = buf;
+    return s;
+}
+
+#define KN_CUDA(call)                                                                      \
+    do {                                                                                   \
+        cudaError_t e_ = (call);                                                           \
+        if (e_ != cudaSuccess)                                                             \
+            return fail(e_ == cudaErrorMemoryAllocation ? KN_ERR_NOMEM : KN_ERR_CUDA,      \
+                        "%s: %s (%s:%d)", #call, cudaGetErrorString(e_), __FILE__, __LINE__); \
+    } while (0)
+
+static inline int pad16(int x) { return (x + 15) & ~15; }
+}  // namespace
+
+namespace kn {
+// ---------------------------------------------------------------------------
+// device buffer helper
+// ---------------------------------------------------------------------------
+struct DevBuf {
+    void* p = nullptr;
+    size_t bytes = 0;
+    ~DevBuf() { release(); }
+    void release() {
+        if (p) cudaFree(p);
+        p = nullptr;
+        bytes = 0;
+    }
+    cudaError_t ensure(size_t b) {
+        if (b <= bytes && p) return cudaSuccess;
+        release();
+        cudaError_t e = cudaMalloc(&p, b ? b : 16);
+        if (e == cudaSuccess) bytes = b;
+        return e;
+    }
+    template <class T> T* as() const { return (T*)p; }
+};
+
+struct Tables {
+    std::unique_ptr<DevBuf> blob;
+    TableLayout tl{};
+    int C = 0, Q = 0, n_fix = 0;
+};
+}  // namespace kn
+
+struct kn_network {
+    int N = 0, R = 0, S_r = 0, S_p = 0;
+    std::vector<double> A, lnk0, tn;
+    std::vector<int> reac, prod, nr, slot0;
+    double nbar = 0, rbar = 0;
+    std::map<std::pair<int, int>, Tables> tables;  // (precision, Q) -> device blob
+    // zone state
+    int Z = 0, capZ = 0;
+    DevBuf Y, T0, rho0, tau, ts, te, dtt, tout, dtn, steps, rej, status;
+    DevBuf key_in, key_out, idx_in, order, cub_tmp, qhead;
+    bool has_const = true;  // conservative until zones are known
+    bool zones_set = false;
+};
+
+namespace {
+
+// ---------------------------------------------------------------------------
+// tables: reactant lists, rate parameters and the flat chunked gather list
+// ---------------------------------------------------------------------------
+static kn_status build_tables(kn_network* n, int prec, int Q, Tables& T) {
+    const int N = n->N, R = n->R;
+    const int zero_idx = R + n->S_r;
+    // rows 0..N-1: F+_i (value index j, once per product slot naming i);
+    // rows N..2N-1: k_i (value index R + reactant slot id naming i)
+    std::vector<std::vector<uint16_t>> rows(2 * N);
+    for (int j = 0; j < R; ++j)
+        for (int q = 0; q < 3; ++q) {
+            int p = n->prod[j * 3 + q];
+            if (p >= 0) rows[p].push_back((uint16_t)j);
+        }
+    for (int j = 0; j < R; ++j)
+        for (int q = 0; q < n->nr[j]; ++q) rows[N + n->reac[j * 3 + q]].push_back((uint16_t)(R + n->slot0[j] + q));
+    std::vector<uint16_t> fidx;
+    std::vector<int> frow, rstart(2 * N), rend(2 * N);
+    for (int r = 0; r < 2 * N; ++r) {
+        if (rows[r].empty()) rows[r].push_back((uint16_t)zero_idx);  // row written as 0
+        rstart[r] = (int)fidx.size();
+        for (uint16_t v : rows[r]) {
+            fidx.push_back(v);
+            frow.push_back(r);
+        }
+        rend[r] = (int)fidx.size() - 1;
+    }
+    const int Tn = (int)fidx.size();
+    const int C = (Tn + Q - 1) / Q;
+    std::vector<uint32_t> terms((size_t)C * Q);
+    for (int c = 0; c < Q; ++c)
+        for (int k = 0; k < C; ++k) {
+            const int p = c * C + k;
+            uint32_t w;
+            if (p < Tn) {
+                const int r = frow[p];
+                w = fidx[p] | ((uint32_t)r << kTermRowShift);
+                if (p == rend[r]) {
+                    w |= kTermEnd;
+                    if (rstart[r] < c * C) w |= kTermHead;
+                }
+            } else {
+                w = (uint32_t)zero_idx;
+            }
+            terms[(size_t)k * Q + c] = w;
+        }
+    std::vector<uint16_t> fix;
+    for (int r = 0; r < 2 * N; ++r) {
+        const int c0 = rstart[r] / C, c1 = rend[r] / C;
+        if (c0 != c1) {
+            fix.push_back((uint16_t)r);
+            fix.push_back((uint16_t)c0);
+            fix.push_back((uint16_t)c1);
+            fix.push_back(0);
+        }
+    }
+    TableLayout tl{};
+    int off = 0;
+    tl.off_A = off;
+    off = pad16(off + 8 * N);
+    tl.off_rspec = off;
+    off = pad16(off + 8 * R);
+    tl.off_rate = off;
+    off = pad16(off + 16 * R);
+    tl.off_terms = off;
+    off = pad16(off + 4 * C * Q);
+    tl.off_fix = off;
+    off = pad16(off + 2 * (int)fix.size());
+    tl.bytes = off;
+    std::vector<unsigned char> blob(off, 0);
+    memcpy(blob.data() + tl.off_A, n->A.data(), 8 * N);
+    for (int j = 0; j < R; ++j) {
+        uint16_t rs[4];
+        rs[0] = (uint16_t)n->reac[j * 3];
+        rs[1] = (uint16_t)(n->nr[j] >= 2 ? n->reac[j * 3 + 1] : N);
+        rs[2] = (uint16_t)(n->nr[j] >= 3 ? n->reac[j * 3 + 2] : N);
+        rs[3] = (uint16_t)(R + n->slot0[j]);
+        memcpy(blob.data() + tl.off_rspec + 8 * j, rs, 8);
+        if (prec == kPrecFP64) {
+            double p[2] = {n->lnk0[j], n->tn[j]};
+            memcpy(blob.data() + tl.off_rate + 16 * j, p, 16);
+        } else {
+            const double a = n->lnk0[j] * 1.4426950408889634;  // log2 units
+            float p[4];
+            p[0] = (float)a;
+            p[1] = (float)(a - (double)p[0]);
+            p[2] = (float)n->tn[j];
+            p[3] = (float)(n->tn[j] - (double)p[2]);
+            memcpy(blob.data() + tl.off_rate + 16 * j, p, 16);
+        }
+    }
+    memcpy(blob.data() + tl.off_terms, terms.data(), 4 * terms.size());
+    if (!fix.empty()) memcpy(blob.data() + tl.off_fix, fix.data(), 2 * fix.size());
+    T.blob.reset(new DevBuf());
+    KN_CUDA(T.blob->ensure(off));
+    KN_CUDA(cudaMemcpy(T.blob->p, blob.data(), off, cudaMemcpyHostToDevice));
+    T.tl = tl;
+    T.C = C;
+    T.Q = Q;
+    T.n_fix = (int)fix.size() / 4;
+    return KN_OK;
+}
+
+static kn_status get_tables(kn_network* n, int prec, int Q, Tables** out) {
+    auto key = std::make_pair(prec, Q);
+    auto it = n->tables.find(key);
+    if (it == n->tables.end()) {
+        Tables T;
+        kn_status s = build_tables(n, prec, Q, T);
+        if (s != KN_OK) return s;
+        it = n->tables.emplace(key, std::move(T)).first;
+    }
+    *out = &it->second;
+    return KN_OK;
+}
+
+static GroupLayout group_layout(const kn_network* n, int prec, int G, bool has_const) {
+    const int real = prec == kPrecFP64 ? 8 : 4;
+    GroupLayout g{};
+    int off = 0;
+    g.off_V = off;
+    off = pad16(off + real * (n->R + n->S_r + 1));
+    g.off_Y64 = off;
+    off = pad16(off + 8 * 2 * (n->N + 1));
+    g.off_Y32 = off;
+    if (prec == kPrecMixed) off = pad16(off + 4 * 2 * (n->N + 1));
+    g.off_Fk = off;
+    off = pad16(off + 8 * 2 * n->N);
+    g.off_carry = off;
+    off = pad16(off + 8 * 2 * G);
+    g.off_kr = off;
+    if (has_const) off = pad16(off + real * n->R);
+    g.off_red = off;
+    off = pad16(off + 8 * 4 * 32 + 16);
+    g.off_state = off;
+    off = pad16(off + (int)sizeof(GroupState));
+    g.bytes = off;
+    return g;
+}
+
+// ---------------------------------------------------------------------------
+// launch configuration
+// ---------------------------------------------------------------------------
+struct DeviceInfo {
+    int dev = -1, sms = 0, smem_optin = 0;
+};
+static DeviceInfo g_dev;
+static int g_smem_limit_set = 0;
+
+static kn_status device_info(DeviceInfo& d) {
+    int dev;
+    KN_CUDA(cudaGetDevice(&dev));
+    if (g_dev.dev != dev) {
+        g_dev.dev = dev;
+        KN_CUDA(cudaDeviceGetAttribute(&g_dev.sms, cudaDevAttrMultiProcessorCount, dev));
+        KN_CUDA(cudaDeviceGetAttribute(&g_dev.smem_optin, cudaDevAttrMaxSharedMemoryPerBlockOptin, dev));
+        g_smem_limit_set = 0;
+    }
+    if (!g_smem_limit_set) {
+        KN_CUDA(integrator_set_smem_limit(g_dev.smem_optin - 1024));
+        g_smem_limit_set = 1;
+    }
+    d = g_dev;
+    return KN_OK;
+}
+
+struct Tiling {
+    int G = 0, M = 0, smem_tables = 1, bytes = 0;
+};
+
+// Smallest usable zone group for a network: one warp for small networks,
+// a warp group (128 threads) otherwise.
+static int base_group(const kn_network* n) { return n->R + n->S_r + n->S_p <= 512 ? 32 : 128; }
+
+// For CTA size P, the tiling of one network: the smallest group size
+// G >= base_group that divides P with at most kMaxGroups groups, preferring
+// tables staged in shared memory; bytes = dynamic shared memory per CTA.
+static kn_status plan_tiling(kn_network* n, int prec, int P, int budget, int G_fixed, Tiling& out, bool& ok) {
+    ok = false;
+    Tiling best;
+    bool have = false;
+    for (int G = G_fixed ? G_fixed : base_group(n); G <= P; G += 32) {
+        if (P % G) continue;
+        const int M = P / G;
+        if (M > kMaxGroups) continue;
+        Tables* tb;
+        kn_status s = get_tables(n, prec, G, &tb);
+        if (s != KN_OK) return s;
+        const GroupLayout gl = group_layout(n, prec, G, n->has_const);
+        if (tb->tl.bytes + M * gl.bytes <= budget) {
+            out = Tiling{G, M, 1, tb->tl.bytes + M * gl.bytes};
+            ok = true;
+            return KN_OK;
+        }
+        if (!have && M * gl.bytes <= budget) {
+            best = Tiling{G, M, 0, M * gl.bytes};
+            have = true;
+        }
+        if (G_fixed) break;
+    }
+    if (have) {
+        out = best;
+        ok = true;
+    }
+    return KN_OK;
+}
+
+struct GraphEntry {
+    cudaGraph_t g = nullptr;
+    cudaGraphExec_t x = nullptr;
+};
+static std::map<std::string, GraphEntry> g_graphs;
+
+}  // namespace
+
+// ===========================================================================
+// C ABI
+// ===========================================================================
+extern "C" {
+
+void kn_default_opts(kn_opts* o) {
+    if (!o) return;
+    memset(o, 0, sizeof *o);
+    o->precision = KN_PREC_MIXED;
+    o->max_reject = 60;
+    o->kappa = 1.0;
+    o->eps_r = 0.05;
+    o->eps_c = 1e-6;
+    o->y_min = 1e-10;
+    o->grow_max = 1.5;
+    o->safety = 0.9;
+    o->shrink = 0.5;
+    o->dt_min_frac = 1e-30;
+    o->max_steps = 10000000;
+    o->use_graph = 0;
+    o->lockstep = 0;
+}
+
+const char* kn_last_error(void) { return g_err.c_str(); }
+
+kn_status kn_create_network(const kn_network_desc* d, kn_network** out) {
+    if (!d || !out) return fail(KN_ERR_INVALID_ARG, "kn_create_network: NULL argument");
+    *out = nullptr;
+    const int N = d->n_species, R = d->n_reactions;
+    if (N < 1 || N > kMaxSpecies) return fail(KN_ERR_INVALID_ARG, "n_species %d outside [1, %d]", N, kMaxSpecies);
+    if (R < 1 || R > 16383) return fail(KN_ERR_INVALID_ARG, "n_reactions %d outside [1, 16383]", R);
+    if (!d->A || !d->reac || !d->prod || !d->ln_k0 || !d->t9_exp)
+        return fail(KN_ERR_INVALID_ARG, "kn_network_desc has a NULL array");
+    std::unique_ptr<kn_network> n(new kn_network());
+    n->N = N;
+    n->R = R;
+    n->A.assign(d->A, d->A + N);
+    for (int i = 0; i < N; ++i)
+        if (!(std::isfinite(n->A[i]) && n->A[i] > 0)) return fail(KN_ERR_INVALID_ARG, "A[%d] must be finite and > 0", i);
+    n->reac.assign(d->reac, d->reac + 3 * R);
+    n->prod.assign(d->prod, d->prod + 3 * R);
+    n->lnk0.assign(d->ln_k0, d->ln_k0 + R);
+    n->tn.assign(d->t9_exp, d->t9_exp + R);
+    n->nr.resize(R);
+    n->slot0.resize(R);
+    int slots = 0, pslots = 0;
+    double nsum = 0, rsum = 0;
+    for (int j = 0; j < R; ++j) {
+        if (!std::isfinite(n->lnk0[j]) || !std::isfinite(n->tn[j]))
+            return fail(KN_ERR_INVALID_ARG, "reaction %d: non-finite rate parameter", j);
+        int c = 0, end = 0;
+        for (int q = 0; q < 3; ++q) {
+            const int s = n->reac[j * 3 + q];
+            if (s < 0) {
+                end = 1;
+                continue;
+            }
+            if (end || s >= N) return fail(KN_ERR_INVALID_ARG, "reaction %d: bad reactant list", j);
+            ++c;
+        }
+        if (c == 0) return fail(KN_ERR_INVALID_ARG, "reaction %d has no reactant", j);
+        int pc = 0;
+        for (int q = 0; q < 3; ++q) {
+            const int s = n->prod[j * 3 + q];
+            if (s >= N) return fail(KN_ERR_INVALID_ARG, "reaction %d: product id out of range", j);
+            if (s >= 0) ++pc;
+        }
+        if (pc == 0) return fail(KN_ERR_INVALID_ARG, "reaction %d has no product", j);
+        n->nr[j] = c;
+        n->slot0[j] = slots;
+        slots += c;
+        pslots += pc;
+        nsum += n->tn[j];
+        rsum += c - 1;
+    }
+    n->S_r = slots;
+    n->S_p = pslots;
+    if (R + slots + 1 > 65535) return fail(KN_ERR_INVALID_ARG, "network too large for 16-bit gather indices");
+    n->nbar = nsum / R;
+    n->rbar = rsum / R;
+    KN_CUDA(n->qhead.ensure(64));
+    *out = n.release();
+    return KN_OK;
+}
+
+kn_status kn_destroy_network(kn_network* net) {
+    if (!net) return KN_OK;
+    cudaDeviceSynchronize();
+    for (auto it = g_graphs.begin(); it != g_graphs.end();) {
+        // graphs may reference this network's buffers: drop them all (cheap to recapture)
+        if (it->second.x) cudaGraphExecDestroy(it->second.x);
+        if (it->second.g) cudaGraphDestroy(it->second.g);
+        it = g_graphs.erase(it);
+    }
+    delete net;
+    return KN_OK;
+}
+
+kn_status kn_network_info(const kn_network* net, int32_t* ns, int32_t* nr, int32_t* srs, int32_t* sps) {
+    if (!net) return fail(KN_ERR_INVALID_ARG, "kn_network_info: NULL network");
+    if (ns) *ns = net->N;
+    if (nr) *nr = net->R;
+    if (srs) *srs = net->S_r;
+    if (sps) *sps = net->S_p;
+    return KN_OK;
+}
+
+kn_status kn_set_zone_conditions(kn_network* n, int32_t Z, const kn_zone_conditions* zc, int32_t mem,
+                                 void* stream_) {
+    if (!n || !zc) return fail(KN_ERR_INVALID_ARG, "kn_set_zone_conditions: NULL argument");
+    if (Z < 1) return fail(KN_ERR_INVALID_ARG, "n_zones must be >= 1");
+    if (mem != KN_MEM_HOST && mem != KN_MEM_DEVICE) return fail(KN_ERR_INVALID_ARG, "bad kn_mem");
+    if (!zc->Y0 || !zc->T0 || !zc->rho0 || !zc->tau || !zc->t_start || !zc->t_end || !zc->dt_trial)
+        return fail(KN_ERR_INVALID_ARG, "kn_zone_conditions has a NULL array");
+    cudaStream_t st = (cudaStream_t)stream_;
+    const int N = n->N;
+    bool has_const = true;
+    if (mem == KN_MEM_HOST) {
+        has_const = false;
+        for (int z = 0; z < Z; ++z) {
+            for (int i = 0; i < N; ++i) {
+                const double y = zc->Y0[(size_t)z * N + i];
+                if (!(std::isfinite(y) && y >= 0))
+                    return fail(KN_ERR_INVALID_ARG, "zone %d: Y0[%d] must be finite and >= 0", z, i);
+            }
+            const double T0 = zc->T0[z], r0 = zc->rho0[z], tau = zc->tau[z], ts = zc->t_start[z],
+                         te = zc->t_end[z], dt = zc->dt_trial[z];
+            if (!(std::isfinite(T0) && T0 > 0 && std::isfinite(r0) && r0 > 0))
+                return fail(KN_ERR_INVALID_ARG, "zone %d: T0 and rho0 must be finite and > 0", z);
+            if (!(std::isfinite(tau) && std::isfinite(ts) && std::isfinite(te) && ts >= 0 && te > ts))
+                return fail(KN_ERR_INVALID_ARG, "zone %d: need finite tau and 0 <= t_start < t_end", z);
+            if (!(std::isfinite(dt) && (ts > 0 || dt > 0)))
+                return fail(KN_ERR_INVALID_ARG, "zone %d: need t_start > 0 or dt_trial > 0", z);
+            if (!(tau > 0)) has_const = true;
+        }
+    }
+    if (Z > n->capZ) {
+        const size_t zd = 8 * (size_t)Z;
+        KN_CUDA(n->Y.ensure(zd * N));
+        KN_CUDA(n->T0.ensure(zd));
+        KN_CUDA(n->rho0.ensure(zd));
+        KN_CUDA(n->tau.ensure(zd));
+        KN_CUDA(n->ts.ensure(zd));
+        KN_CUDA(n->te.ensure(zd));
+        KN_CUDA(n->dtt.ensure(zd));
+        KN_CUDA(n->tout.ensure(zd));
+        KN_CUDA(n->dtn.ensure(zd));
+        KN_CUDA(n->steps.ensure(zd));
+        KN_CUDA(n->rej.ensure(zd));
+        KN_CUDA(n->status.ensure(4 * (size_t)Z));
+        KN_CUDA(n->key_in.ensure(4 * (size_t)Z));
+        KN_CUDA(n->key_out.ensure(4 * (size_t)Z));
+        KN_CUDA(n->idx_in.ensure(4 * (size_t)Z));
+        KN_CUDA(n->order.ensure(4 * (size_t)Z));
+        size_t tmp = 0;
+        KN_CUDA(cub::DeviceRadixSort::SortPairsDescending(nullptr, tmp, (const float*)nullptr, (float*)nullptr,
+                                                          (const int*)nullptr, (int*)nullptr, Z));
+        KN_CUDA(n->cub_tmp.ensure(tmp));
+        n->capZ = Z;
+    }
+    const cudaMemcpyKind kind = mem == KN_MEM_HOST ? cudaMemcpyHostToDevice : cudaMemcpyDeviceToDevice;
+    const size_t zd = 8 * (size_t)Z;
+    KN_CUDA(cudaMemcpyAsync(n->Y.p, zc->Y0, zd * N, kind, st));
+    KN_CUDA(cudaMemcpyAsync(n->T0.p, zc->T0, zd, kind, st));
+    KN_CUDA(cudaMemcpyAsync(n->rho0.p, zc->rho0, zd, kind, st));
+    KN_CUDA(cudaMemcpyAsync(n->tau.p, zc->tau, zd, kind, st));
+    KN_CUDA(cudaMemcpyAsync(n->ts.p, zc->t_start, zd, kind, st));
+    KN_CUDA(cudaMemcpyAsync(n->te.p, zc->t_end, zd, kind, st));
+    KN_CUDA(cudaMemcpyAsync(n->dtt.p, zc->dt_trial, zd, kind, st));
+    KN_CUDA(launch_fill_int(n->status.as<int>(), Z, KN_ZONE_PENDING, st));
+    // work-queue order: predicted longest zones first
+    KN_CUDA(launch_zone_cost_simple(n->T0.as<double>(), n->rho0.as<double>(), Z, n->nbar, n->rbar,
+                                    n->key_in.as<float>(), n->idx_in.as<int>(), st));
+    size_t tmp = n->cub_tmp.bytes;
+    KN_CUDA(cub::DeviceRadixSort::SortPairsDescending(n->cub_tmp.p, tmp, n->key_in.as<float>(),
+                                                      n->key_out.as<float>(), n->idx_in.as<int>(),
+                                                      n->order.as<int>(), Z, 0, 32, st));
+    n->Z = Z;
+    n->has_const = has_const;
+    n->zones_set = true;
+    return KN_OK;
+}
+
+}  // extern "C"
+
+namespace {
+
+static kn_status validate_opts(const kn_opts* o) {
+    if (!o) return fail(KN_ERR_INVALID_ARG, "NULL opts");
+    if (o->precision != KN_PREC_FP64 && o->precision != KN_PREC_MIXED)
+        return fail(KN_ERR_INVALID_ARG, "opts.precision must be KN_PREC_FP64 or KN_PREC_MIXED");
+    if (!(o->kappa > 0 && o->eps_r > 0 && o->eps_c > 0 && o->y_min >= 0 && o->grow_max >= 1 &&
+          o->safety > 0 && o->shrink > 0 && o->shrink < 1 && o->dt_min_frac >= 0 && o->max_steps >= 0 &&
+          o->max_reject >= 0))
+        return fail(KN_ERR_INVALID_ARG, "opts: a controller parameter is out of range");
+    if (o->threads_per_zone && (o->threads_per_zone % 32 || o->threads_per_zone > 1024))
+        return fail(KN_ERR_INVALID_ARG, "opts.threads_per_zone must be a multiple of 32, <= 1024");
+    if (o->threads_per_cta && (o->threads_per_cta % 32 || o->threads_per_cta > 1024))
+        return fail(KN_ERR_INVALID_ARG, "opts.threads_per_cta must be a multiple of 32, <= 1024");
+    if (o->lockstep) return fail(KN_ERR_INVALID_ARG, "opts.lockstep is only used with a learned proposal");
+    if ((o->replay_dt != nullptr) != (o->replay_off != nullptr) ||
+        (o->replay_dt != nullptr) != (o->replay_len != nullptr))
+        return fail(KN_ERR_INVALID_ARG, "opts.replay_dt/off/len must be set together");
+    return KN_OK;
+}
+
+// Fill lp for the listed networks; returns grid/block.
+static kn_status prepare_launch(kn_network* const* nets, int n_nets, const kn_opts* o, LaunchParams& lp,
+                                int& grid, int& block, bool probe) {
+    DeviceInfo di;
+    kn_status s = device_info(di);
+    if (s != KN_OK) return s;
+    const int prec = o->precision;
+    const int budget = di.smem_optin - 1024 - 64;
+    memset(&lp, 0, sizeof lp);
+    lp.n_plans = n_nets;
+    // one CTA size P for the launch; per network the group size G | P
+    Tiling tl[kMaxPlans];
+    int P_best = 0;
+    for (int p = 0; p < n_nets; ++p)
+        if (!nets[p]->zones_set) return fail(KN_ERR_STATE, "network %d has no zones (kn_set_zone_conditions)", p);
+    {
+        int P_lo = 32, P_hi = 1024;
+        if (o->threads_per_cta) P_lo = P_hi = o->threads_per_cta;
+        else if (o->threads_per_zone) P_lo = P_hi = o->threads_per_zone;
+        // without an explicit tiling: the largest CTA that stages every network's tables
+        for (int pass = 0; pass < 2 && !P_best; ++pass) {
+            for (int P = P_hi; P >= P_lo && !P_best; P -= 32) {
+                bool all = true, all_smem = true;
+                Tiling cand[kMaxPlans];
+                for (int p = 0; p < n_nets && all; ++p) {
+                    bool ok;
+                    if ((s = plan_tiling(nets[p], prec, P, budget, o->threads_per_zone, cand[p], ok)) != KN_OK)
+                        return s;
+                    all = ok;
+                    all_smem = all_smem && ok && cand[p].smem_tables;
+                }
+                if (all && (all_smem || pass == 1 || P_lo == P_hi)) {
+                    P_best = P;
+                    for (int p = 0; p < n_nets; ++p) tl[p] = cand[p];
+                }
+            }
+        }
+        if (!P_best) return fail(KN_ERR_INVALID_ARG, "no tiling fits in %d B of shared memory per CTA", budget);
+    }
+    int max_smem = 0;
+    double work[kMaxPlans];
+    double total_work = 0;
+    int zone_base = 0;
+    for (int p = 0; p < n_nets; ++p) {
+        kn_network* n = nets[p];
+        const Tiling t = tl[p];
+        Tables* tb;
+        if ((s = get_tables(n, prec, t.G, &tb)) != KN_OK) return s;
+        const GroupLayout gl = group_layout(n, prec, t.G, n->has_const);
+        PlanDev& P = lp.plans[p];
+        P.blob = (const unsigned char*)tb->blob->p;
+        P.tl = tb->tl;
+        P.N = n->N;
+        P.R = n->R;
+        P.S_r = n->S_r;
+        P.C = tb->C;
+        P.Q = tb->Q;
+        P.n_fix = tb->n_fix;
+        P.zero_idx = n->R + n->S_r;
+        P.smem_tables = t.smem_tables;
+        P.G = t.G;
+        P.M = t.M;
+        P.gl = gl;
+        P.Y = n->Y.as<double>();
+        P.T0 = n->T0.as<double>();
+        P.rho0 = n->rho0.as<double>();
+        P.tau = n->tau.as<double>();
+        P.t_start = n->ts.as<double>();
+        P.t_end = n->te.as<double>();
+        P.dt_trial = n->dtt.as<double>();
+        P.t_out = n->tout.as<double>();
+        P.dt_next = n->dtn.as<double>();
+        P.steps = n->steps.as<long long>();
+        P.rejects = n->rej.as<long long>();
+        P.status = n->status.as<int>();
+        P.n_zones = n->Z;
+        P.zone_base = zone_base;
+        P.order = n->order.as<int>();
+        P.queue_head = n->qhead.as<int>();
+        zone_base += n->Z;
+        max_smem = std::max(max_smem, t.bytes);
+        work[p] = (double)n->Z * (n->R + n->S_r + n->S_p) / (double)t.M;
+        total_work += work[p];
+    }
+    const int max_block = P_best;
+    // one block size for the launch: every plan must fill it exactly
+    block = max_block;
+    for (int p = 0; p < n_nets; ++p)
+        if (lp.plans[p].G * lp.plans[p].M != block)
+            return fail(KN_ERR_INVALID_ARG, "networks in one launch need equal threads per CTA (got %d and %d)",
+                        lp.plans[p].G * lp.plans[p].M, block);
+    lp.smem_bytes = max_smem;
+    int bps = 0;
+    {
+        cudaError_t e = integrator_occupancy(prec, block, max_smem, &bps);
+        if (e != cudaSuccess) return fail(KN_ERR_CUDA, "occupancy: %s", cudaGetErrorString(e));
+    }
+    if (bps < 1) return fail(KN_ERR_INVALID_ARG, "tiling does not fit on an SM (block %d, smem %d)", block, max_smem);
+    grid = di.sms * bps;
+    int zones_total = 0;
+    for (int p = 0; p < n_nets; ++p) zones_total += lp.plans[p].n_zones;
+    if (probe) grid = std::min(grid, std::max(1, zones_total));
+    // home CTAs proportional to each plan's work
+    int b = 0;
+    for (int p = 0; p < n_nets; ++p) {
+        int cnt = (p == n_nets - 1) ? grid - b : (int)std::lround(grid * work[p] / total_work);
+        cnt = std::max(0, std::min(cnt, grid - b));
+        lp.plans[p].cta_begin = b;
+        lp.plans[p].cta_end = b + cnt;
+        b += cnt;
+    }
+    OptsDev& D = lp.o;
+    D.kappa = o->kappa;
+    D.eps_r = o->eps_r;
+    D.eps_c = o->eps_c;
+    D.y_min = o->y_min;
+    D.grow_max = o->grow_max;
+    D.safety = o->safety;
+    D.shrink = o->shrink;
+    D.dt_min_frac = o->dt_min_frac;
+    D.max_steps = o->max_steps;
+    D.max_reject = o->max_reject;
+    D.lockstep = o->lockstep;
+    D.replay_dt = o->replay_dt;
+    D.replay_off = (const long long*)o->replay_off;
+    D.replay_len = (const long long*)o->replay_len;
+    return KN_OK;
+}
+
+static kn_status enqueue(kn_network* const* nets, int n_nets, const LaunchParams& lp, int prec, int grid,
+                         int block, cudaStream_t st) {
+    for (int p = 0; p < n_nets; ++p) KN_CUDA(cudaMemsetAsync(nets[p]->qhead.p, 0, sizeof(int), st));
+    KN_CUDA(launch_integrator(lp, prec, grid, block, st));
+    return KN_OK;
+}
+
+}  // namespace
+
+extern "C" {
+
+kn_status kn_integrate_batch(kn_network* const* nets, int32_t n_nets, const kn_opts* o, void* stream_) {
+    if (!nets || n_nets < 1 || n_nets > kMaxPlans)
+        return fail(KN_ERR_INVALID_ARG, "need 1..%d networks", kMaxPlans);
+    for (int p = 0; p < n_nets; ++p) {
+        if (!nets[p]) return fail(KN_ERR_INVALID_ARG, "network %d is NULL", p);
+        for (int q = 0; q < p; ++q)
+            if (nets[q] == nets[p]) return fail(KN_ERR_INVALID_ARG, "networks must be distinct");
+    }
+    kn_status s = validate_opts(o);
+    if (s != KN_OK) return s;
+    if (o->mlp) return fail(KN_ERR_INVALID_ARG, "learned proposal not available in this entry point");
+    cudaStream_t st = (cudaStream_t)stream_;
+    LaunchParams lp;
+    int grid, block;
+    if ((s = prepare_launch(nets, n_nets, o, lp, grid, block, false)) != KN_OK) return s;
+    if (!o->use_graph) return enqueue(nets, n_nets, lp, o->precision, grid, block, st);
+    // CUDA graph keyed by the full launch description
+    std::string key((const char*)&lp, sizeof lp);
+    key.append((const char*)&grid, sizeof grid);
+    key.append((const char*)&block, sizeof block);
+    key.append((const char*)&o->precision, sizeof o->precision);
+    auto it = g_graphs.find(key);
+    if (it == g_graphs.end()) {
+        if (g_graphs.size() >= 32) {
+            for (auto& kv : g_graphs) {
+                if (kv.second.x) cudaGraphExecDestroy(kv.second.x);
+                if (kv.second.g) cudaGraphDestroy(kv.second.g);
+            }
+            g_graphs.clear();
+        }
+        cudaStream_t cs;
+        KN_CUDA(cudaStreamCreateWithFlags(&cs, cudaStreamNonBlocking));
+        GraphEntry ge;
+        cudaError_t e = cudaStreamBeginCapture(cs, cudaStreamCaptureModeThreadLocal);
+        if (e == cudaSuccess) {
+            kn_status es = enqueue(nets, n_nets, lp, o->precision, grid, block, cs);
+            e = cudaStreamEndCapture(cs, &ge.g);
+            if (es != KN_OK) {
+                cudaStreamDestroy(cs);
+                return es;
+            }
+        }
+        cudaStreamDestroy(cs);
+        if (e != cudaSuccess) return fail(KN_ERR_CUDA, "graph capture: %s", cudaGetErrorString(e));
+        KN_CUDA(cudaGraphInstantiate(&ge.x, ge.g, 0));
+        it = g_graphs.emplace(key, ge).first;
+    }
+    KN_CUDA(cudaGraphLaunch(it->second.x, st));
+    return KN_OK;
+}
+
+kn_status kn_probe_step(kn_network* net, const kn_opts* o, double* Fp, double* k, double* Y1, double* cons,
+                        double* rel, void* stream_) {
+    if (!net) return fail(KN_ERR_INVALID_ARG, "kn_probe_step: NULL network");
+    kn_status s = validate_opts(o);
+    if (s != KN_OK) return s;
+    if (!net->zones_set) return fail(KN_ERR_STATE, "kn_probe_step: no zones set");
+    cudaStream_t st = (cudaStream_t)stream_;
+    const size_t zn = 8 * (size_t)net->Z * net->N, zd = 8 * (size_t)net->Z;
+    // outputs the caller did not ask for go to scratch
+    DevBuf scratch;
+    KN_CUDA(scratch.ensure(3 * zn + 2 * zd));
+    double* sp = scratch.as<double>();
+    kn_opts oo = *o;
+    oo.replay_dt = nullptr;
+    oo.replay_off = nullptr;
+    oo.replay_len = nullptr;
+    LaunchParams lp;
+    int grid, block;
+    kn_network* nets[1] = {net};
+    if ((s = prepare_launch(nets, 1, &oo, lp, grid, block, true)) != KN_OK) return s;
+    lp.o.probe = 1;
+    lp.o.probe_Fp = Fp ? Fp : sp;
+    lp.o.probe_k = k ? k : sp + zn / 8;
+    lp.o.probe_Y1 = Y1 ? Y1 : sp + 2 * zn / 8;
+    lp.o.probe_cons = cons ? cons : sp + 3 * zn / 8;
+    lp.o.probe_rel = rel ? rel : sp + 3 * zn / 8 + zd / 8;
+    if ((s = enqueue(nets, 1, lp, o->precision, grid, block, st)) != KN_OK) return s;
+    KN_CUDA(cudaStreamSynchronize(st));  // scratch is freed on return
+    return KN_OK;
+}
+
+kn_status kn_get_abundances(const kn_network* n, double* Y, double* t, double* dt_next, int64_t* steps,
+                            int64_t* rejects, int32_t* status, int32_t mem, void* stream_) {
+    if (!n) return fail(KN_ERR_INVALID_ARG, "kn_get_abundances: NULL network");
+    if (mem != KN_MEM_HOST && mem != KN_MEM_DEVICE) return fail(KN_ERR_INVALID_ARG, "bad kn_mem");
+    if (!n->zones_set) return fail(KN_ERR_STATE, "kn_get_abundances: no zones set");
+    cudaStream_t st = (cudaStream_t)stream_;
+    const cudaMemcpyKind kind = mem == KN_MEM_HOST ? cudaMemcpyDeviceToHost : cudaMemcpyDeviceToDevice;
+    const size_t zd = 8 * (size_t)n->Z;
+    if (Y) KN_CUDA(cudaMemcpyAsync(Y, n->Y.p, zd * n->N, kind, st));
+    if (t) KN_CUDA(cudaMemcpyAsync(t, n->tout.p, zd, kind, st));
+    if (dt_next) KN_CUDA(cudaMemcpyAsync(dt_next, n->dtn.p, zd, kind, st));
+    if (steps) KN_CUDA(cudaMemcpyAsync(steps, n->steps.p, zd, kind, st));
+    if (rejects) KN_CUDA(cudaMemcpyAsync(rejects, n->rej.p, zd, kind, st));
+    if (status) KN_CUDA(cudaMemcpyAsync(status, n->status.p, 4 * (size_t)n->Z, kind, st));
+    KN_CUDA(cudaStreamSynchronize(st));
+    return KN_OK;
+}
+
+kn_status kn_get_batch_stats(kn_network* const* nets, int32_t n_nets, void* stream_, kn_batch_stats* stats) {
+    if (!nets || n_nets < 1 || !stats) return fail(KN_ERR_INVALID_ARG, "kn_get_batch_stats: bad arguments");
+    memset(stats, 0, sizeof *stats);
+    for (int p = 0; p < n_nets; ++p) {
+        const kn_network* n = nets[p];
+        if (!n || !n->zones_set) return fail(KN_ERR_STATE, "network %d has no zones", p);
+        std::vector<int64_t> st(n->Z), rj(n->Z);
+        std::vector<int32_t> ss(n->Z);
+        kn_status s = kn_get_abundances(n, nullptr, nullptr, nullptr, st.data(), rj.data(), ss.data(),
+                                        KN_MEM_HOST, stream_);
+        if (s != KN_OK) return s;
+        for (int z = 0; z < n->Z; ++z) {
+            stats->zones += 1;
+            stats->zones_ok += ss[z] == KN_ZONE_OK;
+            stats->steps += st[z];
+            stats->rejects += rj[z];
+        }
+    }
+    return KN_OK;
+}
+
+}  // extern "C"

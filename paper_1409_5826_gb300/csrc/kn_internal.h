@@ -1,0 +1,129 @@
+// kn_internal.h -- library-internal layouts shared by the host runtime and the
+// integrator kernel.  Nothing here is part of the C ABI (include/kn.h).
+#pragma once
+
+#include <cstdint>
+#include <cuda_runtime.h>
+
+namespace kn {
+
+// Term encoding of the flat gather list (one 32-bit word per term):
+//   bits  0..15  index into the zone's value array V (a flux f_j, a reactant-
+//                slot partial, or the constant-zero entry)
+//   bits 16..26  output row: 0..N-1 are F+_i, N..2N-1 are k_i
+//   bit  27      END: the row's last term inside this chunk
+//   bit  28      HEAD: the row began in an earlier chunk (write to the carry)
+constexpr uint32_t kTermRowShift = 16;
+constexpr uint32_t kTermRowMask = 0x7ffu;
+constexpr uint32_t kTermEnd = 1u << 27;
+constexpr uint32_t kTermHead = 1u << 28;
+
+constexpr int kMaxSpecies = 1023;
+constexpr int kMaxPlans = 4;      // networks per launch
+constexpr int kMaxGroups = 15;    // named barriers 1..15
+constexpr int kPrecFP64 = 0;
+constexpr int kPrecMixed = 1;
+
+// One network's tables, as one contiguous device blob per precision; the
+// kernel stages the blob into shared memory when it fits.
+struct TableLayout {
+    int32_t bytes;        // total (multiple of 16)
+    int32_t off_A;        // double[N]
+    int32_t off_rspec;    // ushort4[R]: reactant species a, b, c (N = none), V index of slot 0
+    int32_t off_rate;     // FP64: double2[R] (ln k0, n); mixed: float4[R] (a_hi, a_lo, n_hi, n_lo), log2 units
+    int32_t off_terms;    // uint32[Q * C], chunk-major (term k of chunk c at k*Q + c)
+    int32_t off_fix;      // ushort4[n_fix]: (row, first chunk, last chunk, 0)
+};
+
+// Per-group shared-memory layout (byte offsets inside one group's region).
+struct GroupLayout {
+    int32_t bytes;
+    int32_t off_V;      // real[R + S_r + 1]; last entry is a constant 0
+    int32_t off_Y64;    // double[2][N + 1]; entry N is the constant 1 (product sentinel)
+    int32_t off_Y32;    // float[2][N + 1] (mixed only)
+    int32_t off_Fk;     // double[2N]: F+ then k
+    int32_t off_carry;  // double[2][Q]: head carries then tail carries
+    int32_t off_kr;     // real[R]: rates of a constant-condition zone
+    int32_t off_red;    // double[4 * 32] reduction scratch
+    int32_t off_state;  // GroupState
+};
+
+struct GroupState {
+    double t, dt, t_end, h;
+    double lnT, lnR;          // ln T9, ln rho at the current step start
+    double T0, rho0, tau;
+    double cons, rel_num, rel_den;
+    long long steps, rejects;
+    int zone, status, nrej, rhs_valid;
+    int cur, done, finite, clipped;
+    int constant, accept, pad0, pad1;
+};
+
+struct PlanDev {
+    // tables
+    const unsigned char* blob;  // device
+    TableLayout tl;
+    int32_t N, R, S_r, C, Q, n_fix;
+    int32_t zero_idx;            // V index of the constant zero (= R + S_r)
+    int32_t smem_tables;         // 1: stage blob into shared memory
+    int32_t G, M;                // threads per zone group, groups per CTA
+    GroupLayout gl;
+    // zone state (device, library-owned)
+    double* Y;                   // [Z][N] in: Y0, out: Y at t
+    const double* T0;
+    const double* rho0;
+    const double* tau;
+    const double* t_start;
+    const double* t_end;
+    const double* dt_trial;
+    double* t_out;
+    double* dt_next;
+    long long* steps;
+    long long* rejects;
+    int* status;
+    int32_t n_zones;
+    int32_t zone_base;           // first global zone index of this plan (replay arrays)
+    const int* order;            // work-queue order of zones (longest first)
+    int* queue_head;             // work-queue counter (reset to 0 before each launch)
+    int32_t cta_begin, cta_end;  // CTAs whose home is this plan
+};
+
+struct OptsDev {
+    double kappa, eps_r, eps_c, y_min, grow_max, safety, shrink, dt_min_frac;
+    long long max_steps;
+    int max_reject;
+    int lockstep;
+    // replay
+    const double* replay_dt;
+    const long long* replay_off;
+    const long long* replay_len;
+    // probe (one step, no test): outputs [zones][N] / [zones]
+    double* probe_Fp;
+    double* probe_k;
+    double* probe_Y1;
+    double* probe_cons;
+    double* probe_rel;
+    int probe;
+};
+
+struct LaunchParams {
+    int32_t n_plans;
+    int32_t smem_bytes;
+    PlanDev plans[kMaxPlans];
+    OptsDev o;
+};
+
+// Host-side launch of the integrator kernel (kn_integrate.cu).
+cudaError_t launch_integrator(const LaunchParams& lp, int precision, int grid, int block,
+                              cudaStream_t stream);
+// Occupancy query for a given precision, block size and shared memory.
+cudaError_t integrator_occupancy(int precision, int block, int smem, int* blocks_per_sm);
+// Enable the large dynamic shared memory carve-out for both kernel variants.
+cudaError_t integrator_set_smem_limit(int bytes);
+// Work-queue ordering key per zone (mean log-rate at the initial conditions)
+// and the identity permutation, for a descending sort.
+cudaError_t launch_zone_cost_simple(const double* T0, const double* rho0, int n, double nbar,
+                                    double rbar, float* key, int* idx, cudaStream_t stream);
+cudaError_t launch_fill_int(int* p, int n, int v, cudaStream_t stream);
+
+}  // namespace kn

@@ -1,0 +1,247 @@
+"""ctypes binding of libkn (include/kn.h): argument marshalling only.
+
+Every step of the integration runs in the library's CUDA kernels.  Host
+arrays are numpy; device arrays are torch CUDA tensors (torch supplies device
+memory and the current stream, nothing else).  If libkn.so is missing or does
+not load, every entry point raises KnError: there is no CPU fallback.
+"""
+from __future__ import annotations
+
+import ctypes as C
+import os
+import re
+from dataclasses import dataclass, fields
+
+import numpy as np
+
+HERE = os.path.dirname(os.path.abspath(__file__))
+LIB_PATH = os.path.join(HERE, "libkn.so")
+HEADER = os.path.join(os.path.dirname(HERE), "include", "kn.h")
+
+KN_OK, KN_ERR_INVALID_ARG, KN_ERR_CUDA, KN_ERR_NOMEM, KN_ERR_STATE = range(5)
+ZONE_STATUS = {0: "ok", 1: "step_limit", 2: "dt_underflow", 3: "nonfinite", 4: "max_reject",
+               5: "invalid", 6: "pending"}
+PREC_FP64, PREC_MIXED = 0, 1
+MEM_HOST, MEM_DEVICE = 0, 1
+
+
+class KnError(RuntimeError):
+    def __init__(self, code, msg):
+        super().__init__(f"libkn error {code}: {msg}")
+        self.code = code
+
+
+class _Desc(C.Structure):
+    _fields_ = [("n_species", C.c_int32), ("n_reactions", C.c_int32), ("A", C.c_void_p),
+                ("reac", C.c_void_p), ("prod", C.c_void_p), ("ln_k0", C.c_void_p),
+                ("t9_exp", C.c_void_p)]
+
+
+class _Zones(C.Structure):
+    _fields_ = [(n, C.c_void_p) for n in ("Y0", "T0", "rho0", "tau", "t_start", "t_end", "dt_trial")]
+
+
+class _Opts(C.Structure):
+    _fields_ = [("precision", C.c_int32), ("max_reject", C.c_int32), ("kappa", C.c_double),
+                ("eps_r", C.c_double), ("eps_c", C.c_double), ("y_min", C.c_double),
+                ("grow_max", C.c_double), ("safety", C.c_double), ("shrink", C.c_double),
+                ("dt_min_frac", C.c_double), ("max_steps", C.c_int64),
+                ("threads_per_cta", C.c_int32), ("threads_per_zone", C.c_int32),
+                ("use_graph", C.c_int32), ("lockstep", C.c_int32),
+                ("replay_dt", C.c_void_p), ("replay_off", C.c_void_p), ("replay_len", C.c_void_p),
+                ("mlp", C.c_void_p), ("reserved", C.c_int64 * 8)]
+
+
+class _Stats(C.Structure):
+    _fields_ = [("zones", C.c_int64), ("zones_ok", C.c_int64), ("steps", C.c_int64),
+                ("rejects", C.c_int64), ("proposals_used", C.c_int64)]
+
+
+_lib = None
+
+
+def lib():
+    """Load libkn.so (built by paper_1409_5826_gb300.build); raise if absent."""
+    global _lib
+    if _lib is not None:
+        return _lib
+    if not os.path.exists(LIB_PATH):
+        raise KnError(-1, f"{LIB_PATH} is not built: run paper_1409_5826_gb300.build.build() "
+                          "(nvcc, sm_103a); there is no CPU fallback")
+    L = C.CDLL(LIB_PATH)
+    P, I32, I64 = C.c_void_p, C.c_int32, C.c_int64
+    sig = {
+        "kn_default_opts": (None, [C.POINTER(_Opts)]),
+        "kn_last_error": (C.c_char_p, []),
+        "kn_create_network": (I32, [C.POINTER(_Desc), C.POINTER(P)]),
+        "kn_destroy_network": (I32, [P]),
+        "kn_network_info": (I32, [P, P, P, P, P]),
+        "kn_set_zone_conditions": (I32, [P, I32, C.POINTER(_Zones), I32, P]),
+        "kn_integrate_batch": (I32, [P, I32, C.POINTER(_Opts), P]),
+        "kn_get_abundances": (I32, [P, P, P, P, P, P, P, I32, P]),
+        "kn_get_batch_stats": (I32, [P, I32, P, C.POINTER(_Stats)]),
+        "kn_probe_step": (I32, [P, C.POINTER(_Opts), P, P, P, P, P, P]),
+    }
+    for name, (res, args) in sig.items():
+        f = getattr(L, name)
+        f.restype = res
+        f.argtypes = args
+    _lib = L
+    return L
+
+
+def header_functions():
+    """Names of every function declared in include/kn.h."""
+    txt = open(HEADER).read()
+    txt = re.sub(r"/\*.*?\*/", "", txt, flags=re.S)
+    return sorted(set(re.findall(r"\b(kn_[a-z0-9_]+)\s*\(", txt)))
+
+
+def _check(code):
+    if code != KN_OK:
+        raise KnError(code, lib().kn_last_error().decode())
+
+
+def _stream_ptr(stream=None):
+    if stream is None:
+        import torch
+        return torch.cuda.current_stream().cuda_stream
+    return int(getattr(stream, "cuda_stream", stream))
+
+
+@dataclass
+class Opts:
+    precision: int = PREC_MIXED
+    max_reject: int = 60
+    kappa: float = 1.0
+    eps_r: float = 0.05
+    eps_c: float = 1e-6
+    y_min: float = 1e-10
+    grow_max: float = 1.5
+    safety: float = 0.9
+    shrink: float = 0.5
+    dt_min_frac: float = 1e-30
+    max_steps: int = 10_000_000
+    threads_per_cta: int = 0
+    threads_per_zone: int = 0
+    use_graph: int = 0
+    lockstep: int = 0
+    replay_dt: int = 0
+    replay_off: int = 0
+    replay_len: int = 0
+    mlp: int = 0
+
+    def c(self) -> _Opts:
+        o = _Opts()
+        lib().kn_default_opts(C.byref(o))
+        for f in fields(self):
+            v = getattr(self, f.name)
+            setattr(o, f.name, (v or None) if f.name in ("replay_dt", "replay_off", "replay_len", "mlp") else v)
+        return o
+
+
+def default_opts() -> _Opts:
+    o = _Opts()
+    lib().kn_default_opts(C.byref(o))
+    return o
+
+
+def _host(a, dtype):
+    return np.ascontiguousarray(a, dtype=dtype)
+
+
+class Network:
+    """A network resident on the current device, plus its zones' state."""
+
+    def __init__(self, net):
+        self.N = int(net.n_species)
+        self.R = int(net.n_reactions)
+        self._keep = [_host(net.A, np.float64), _host(net.reac, np.int32), _host(net.prod, np.int32),
+                      _host(net.ln_k0, np.float64), _host(net.t9_exp, np.float64)]
+        d = _Desc(self.N, self.R, *[a.ctypes.data for a in self._keep])
+        h = C.c_void_p()
+        _check(lib().kn_create_network(C.byref(d), C.byref(h)))
+        self.h = h
+        self.Z = 0
+
+    def info(self):
+        v = [C.c_int32() for _ in range(4)]
+        _check(lib().kn_network_info(self.h, *[C.byref(x) for x in v]))
+        return dict(n_species=v[0].value, n_reactions=v[1].value, reactant_slots=v[2].value,
+                    product_slots=v[3].value)
+
+    def close(self):
+        if getattr(self, "h", None):
+            lib().kn_destroy_network(self.h)
+            self.h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def set_zones(self, zones, stream=None):
+        """zones: kn_inputs.Zones (host numpy) or a dict of torch CUDA tensors
+        with keys Y0, T0, rho0, tau, t_start, t_end, dt_trial."""
+        names = ("Y0", "T0", "rho0", "tau", "t_start", "t_end", "dt_trial")
+        if isinstance(zones, dict):
+            ts = [zones[n] for n in names]
+            for t in ts:
+                if not (t.is_cuda and t.is_contiguous()) or t.dtype.itemsize != 8:
+                    raise ValueError("device zone arrays must be contiguous float64 CUDA tensors")
+            Z = int(ts[1].shape[0])
+            zc = _Zones(*[t.data_ptr() for t in ts])
+            mem = MEM_DEVICE
+            self._zkeep = ts
+        else:
+            arrs = [_host(getattr(zones, n), np.float64) for n in names]
+            Z = int(arrs[1].shape[0])
+            zc = _Zones(*[a.ctypes.data for a in arrs])
+            mem = MEM_HOST
+            self._zkeep = arrs
+        _check(lib().kn_set_zone_conditions(self.h, Z, C.byref(zc), mem, C.c_void_p(_stream_ptr(stream))))
+        self.Z = Z
+
+    def get(self, stream=None):
+        """Copy the results to host numpy arrays (synchronises the stream)."""
+        Z, N = self.Z, self.N
+        out = dict(Y=np.empty((Z, N)), t=np.empty(Z), dt_next=np.empty(Z),
+                   steps=np.empty(Z, np.int64), rejects=np.empty(Z, np.int64),
+                   status=np.empty(Z, np.int32))
+        _check(lib().kn_get_abundances(self.h, *[out[k].ctypes.data for k in
+                                                 ("Y", "t", "dt_next", "steps", "rejects", "status")],
+                                       MEM_HOST, C.c_void_p(_stream_ptr(stream))))
+        return out
+
+    def get_device(self, out: dict, stream=None):
+        """Copy the results into caller-owned torch CUDA tensors (keys as in get())."""
+        keys = ("Y", "t", "dt_next", "steps", "rejects", "status")
+        ptrs = [out[k].data_ptr() if k in out else None for k in keys]
+        _check(lib().kn_get_abundances(self.h, *ptrs, MEM_DEVICE, C.c_void_p(_stream_ptr(stream))))
+        return out
+
+    def probe(self, opts: Opts, stream=None):
+        """One step from each zone's initial state (no accept test): F+, k, Y1, cons, rel."""
+        import torch
+        Z, N = self.Z, self.N
+        dev = torch.device("cuda", torch.cuda.current_device())
+        o = {k: torch.empty((Z, N) if k in ("Fp", "k", "Y1") else (Z,), dtype=torch.float64, device=dev)
+             for k in ("Fp", "k", "Y1", "cons", "rel")}
+        _check(lib().kn_probe_step(self.h, C.byref(opts.c()), *[o[k].data_ptr() for k in
+                                                                ("Fp", "k", "Y1", "cons", "rel")],
+                                   C.c_void_p(_stream_ptr(stream))))
+        return {k: v.cpu().numpy() for k, v in o.items()}
+
+
+def integrate_batch(nets, opts: Opts, stream=None):
+    """Enqueue the integration of every zone of every network (asynchronous)."""
+    arr = (C.c_void_p * len(nets))(*[n.h for n in nets])
+    _check(lib().kn_integrate_batch(arr, len(nets), C.byref(opts.c()), C.c_void_p(_stream_ptr(stream))))
+
+
+def batch_stats(nets, stream=None) -> dict:
+    arr = (C.c_void_p * len(nets))(*[n.h for n in nets])
+    s = _Stats()
+    _check(lib().kn_get_batch_stats(arr, len(nets), C.c_void_p(_stream_ptr(stream)), C.byref(s)))
+    return {f: getattr(s, f) for f, _ in _Stats._fields_}

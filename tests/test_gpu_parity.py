@@ -1,0 +1,353 @@
+"""GPU parity: the CUDA path (through the C ABI) against the CPU FP64 oracle.
+
+Tiers:
+  1. one step from identical state (kn_probe_step): F+, k_i, Y' and the error
+     measures, element by element;
+  2. replayed dt: the GPU takes exactly the oracle's accepted dt sequence;
+     end states compared element by element;
+  3. free-running: the GPU's own controller against the oracle's; end states,
+     step counts and statuses.
+Tolerances (relative, on the abundances the accept test looks at, Y > 1e-10):
+  FP64 path:  1e-12 one step; 1e-9 replayed (the FP64 bar); free-running 10*eps_r.
+  Mixed path: 1e-5 one step; 1e-4 replayed; free-running 10*eps_r.
+The FP64 one-step bound comes from rounding: the oracle evaluates
+k0 T9^n rho^(r-1) with pow and sums without FMA, the GPU evaluates
+exp(ln k0 + n ln T9 + (r-1) ln rho) with FMA, a few ulp apart per term.
+The mixed bound comes from FP32 rates/fluxes (~4 ulp = 5e-7 per flux) and
+Kahan-compensated FP32 gathers.
+"""
+import math
+
+import numpy as np
+import pytest
+
+from kn_inputs import (Zones, chain_network, constant_zones, custom_network, net150, net365,
+                       profile_zones, random_tiny_network)
+
+pytestmark = pytest.mark.gpu
+
+FP64, MIXED = 0, 1
+TOL_STEP = {FP64: 1e-12, MIXED: 1e-5}  # Y' on the scale max(Y, Y')
+TOL_REPLAY = {FP64: 1e-9, MIXED: 1e-4}
+
+
+@pytest.fixture(scope="module")
+def kn():
+    import torch
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+    from paper_1409_5826_gb300 import build, kn as knmod
+    build.build()
+    return knmod
+
+
+def _rel_err(a, b, floor):
+    m = np.abs(b) > floor
+    if not m.any():
+        return 0.0
+    return float(np.max(np.abs(a[m] - b[m]) / np.abs(b[m])))
+
+
+def _random_states(net, Z, seed):
+    """Random abundance vectors spanning 1e-14..1 with sum A Y = 1 and some zeros."""
+    rng = np.random.default_rng(seed)
+    Y = 10.0 ** rng.uniform(-14, 0, (Z, net.n_species))
+    Y[rng.uniform(size=Y.shape) < 0.1] = 0.0
+    Y /= (Y * net.A).sum(1, keepdims=True)
+    return Y
+
+
+def _zones_with(net, Y, T0, rho0, tau, t_start, dt):
+    Z = Y.shape[0]
+    f = lambda v: np.full(Z, float(v)) if np.isscalar(v) else np.asarray(v, float)
+    return Zones(Y0=Y, T0=f(T0), rho0=f(rho0), tau=f(tau), t_start=f(t_start), t_end=f(1.0),
+                 dt_trial=f(dt))
+
+
+# --------------------------------------------------------------------------
+# tier 1: one step
+# --------------------------------------------------------------------------
+TILINGS = [(0, 0), (32, 32), (64, 128), (128, 256), (256, 256)]
+
+
+@pytest.mark.parametrize("prec", [FP64, MIXED])
+@pytest.mark.parametrize("factory", [chain_network, net150, net365])
+@pytest.mark.parametrize("tiling", TILINGS)
+def test_one_step_parity(kn, oracle_mod, prec, factory, tiling):
+    net = factory()
+    orc = oracle_mod.Oracle(net)
+    Z = 37  # not a multiple of any group count: ragged last wave
+    Y = _random_states(net, Z, 5)
+    rng = np.random.default_rng(1)
+    T0 = rng.uniform(2, 7, Z)
+    rho0 = 10 ** rng.uniform(7, 9, Z)
+    tau = np.where(np.arange(Z) % 3 == 0, 0.0, 10 ** rng.uniform(-1, 0, Z))  # some constant zones
+    ts = 10 ** rng.uniform(-12, -9, Z)
+    dt = 10 ** rng.uniform(-16, -9, Z)
+    z = _zones_with(net, Y, T0, rho0, tau, ts, dt)
+    g = kn.Network(net)
+    g.set_zones(z)
+    G, P = tiling
+    out = g.probe(kn.Opts(precision=prec, threads_per_zone=G, threads_per_cta=P))
+    tol = TOL_STEP[prec]
+    for i in range(Z):
+        T9, rho = orc.conditions(T0[i], rho0[i], tau[i], ts[i])
+        k = orc.rates(T9, rho)
+        Fp, kk, _ = orc.rhs(k, Y[i])
+        Yn, _ = orc.update(Y[i], Fp, kk, dt[i])
+        floor = 1e-300 if prec == FP64 else 1e-30 * max(Fp.max(), 1e-300)
+        assert _rel_err(out["Fp"][i], Fp, floor) < tol, ("F+", i)
+        floor = 1e-300 if prec == FP64 else 1e-30 * max(kk.max(), 1e-300)
+        assert _rel_err(out["k"][i], kk, floor) < tol, ("k", i)
+        # Y' error measured on the accept test's scale, max(Y, Y'): the mixed
+        # path's ~1e-6 error in k_i is amplified by 1/(1 - k dt) in Y' itself
+        # for forward-Euler species near the switch
+        scale = np.maximum(Y[i], Yn)
+        m = scale > (1e-30 if prec == FP64 else 1e-10)
+        assert np.max(np.abs(out["Y1"][i][m] - Yn[m]) / scale[m]) < tol, ("Y1", i)
+        acc, cons, rel, fin = orc.test(Y[i], Yn)
+        gross = np.sum(np.abs(net.A * (Yn - Y[i])))
+        assert abs(out["cons"][i] - cons) <= 10 * tol * gross + 1e-15, ("cons", i)
+        assert abs(out["rel"][i] - rel) <= (1e-10 if prec == FP64 else 10 * tol), ("rel", i)
+
+
+# --------------------------------------------------------------------------
+# tier 2: replayed dt sequences
+# --------------------------------------------------------------------------
+def _replay(kn, net, zones, dts_list, prec, tiling=(0, 0)):
+    import torch
+    g = kn.Network(net)
+    g.set_zones(zones)
+    lens = np.array([len(d) for d in dts_list], np.int64)
+    off = np.concatenate([[0], np.cumsum(lens)[:-1]]).astype(np.int64)
+    flat = np.concatenate(dts_list) if lens.sum() else np.zeros(1)
+    dev = torch.device("cuda")
+    t_dt = torch.from_numpy(flat).to(dev)
+    t_off = torch.from_numpy(off).to(dev)
+    t_len = torch.from_numpy(lens).to(dev)
+    o = kn.Opts(precision=prec, replay_dt=t_dt.data_ptr(), replay_off=t_off.data_ptr(),
+                replay_len=t_len.data_ptr(), threads_per_zone=tiling[0], threads_per_cta=tiling[1])
+    kn.integrate_batch([g], o)
+    r = g.get()
+    del t_dt, t_off, t_len
+    return r
+
+
+@pytest.mark.parametrize("prec", [FP64, MIXED])
+def test_replay_parity_150(kn, oracle_mod, prec):
+    net = net150()
+    orc = oracle_mod.Oracle(net)
+    z = profile_zones(net, 6, t_end=1e-10)
+    rec = [orc.integrate(z, i, record=10 ** 6) for i in range(6)]
+    r = _replay(kn, net, z, [x["dts"] for x in rec], prec)
+    for i in range(6):
+        assert r["status"][i] == 0 and r["steps"][i] == rec[i]["steps"]
+        assert r["t"][i] == rec[i]["t"]
+        err = _rel_err(r["Y"][i], rec[i]["Y"], 1e-10)
+        assert err < TOL_REPLAY[prec], (i, err)
+
+
+@pytest.mark.parametrize("prec", [FP64, MIXED])
+def test_replay_parity_chain_full_interval(kn, oracle_mod, prec):
+    net = chain_network()
+    orc = oracle_mod.Oracle(net)
+    z = constant_zones(net)  # T9 = 3, rho = 1e8, t 1e-12 -> 1e-2
+    rec = orc.integrate(z, 0, record=10 ** 6)
+    r = _replay(kn, net, z, [rec["dts"]], prec)
+    assert r["steps"][0] == rec["steps"]
+    assert _rel_err(r["Y"][0], rec["Y"], 1e-10) < TOL_REPLAY[prec]
+
+
+@pytest.mark.parametrize("prec", [FP64, MIXED])
+def test_replay_parity_365(kn, oracle_mod, prec):
+    net = net365()
+    orc = oracle_mod.Oracle(net)
+    z = profile_zones(net, 3, t_end=3e-11)
+    rec = [orc.integrate(z, i, record=10 ** 6) for i in range(3)]
+    r = _replay(kn, net, z, [x["dts"] for x in rec], prec)
+    for i in range(3):
+        assert _rel_err(r["Y"][i], rec[i]["Y"], 1e-10) < TOL_REPLAY[prec]
+
+
+# --------------------------------------------------------------------------
+# tier 3: free-running controller
+# --------------------------------------------------------------------------
+@pytest.mark.parametrize("prec", [FP64, MIXED])
+def test_free_running_150(kn, oracle_mod, prec):
+    net = net150()
+    orc = oracle_mod.Oracle(net)
+    Z = 24
+    z = profile_zones(net, Z, t_end=1e-10)
+    ref = orc.integrate_batch(z, threads=8)
+    g = kn.Network(net)
+    g.set_zones(z)
+    kn.integrate_batch([g], kn.Opts(precision=prec))
+    r = g.get()
+    assert (r["status"] == 0).all() and np.array_equal(r["t"], z.t_end)
+    assert (r["Y"] >= 0).all()
+    for i in range(Z):
+        assert _rel_err(r["Y"][i], ref["Y"][i], 1e-10) < 10 * 0.05
+    ratio = r["steps"].sum() / ref["steps"].sum()
+    assert abs(ratio - 1) < 0.02, ratio
+    drift = np.abs((r["Y"] * net.A).sum(1) - 1)
+    assert (drift <= r["steps"] * 1e-6).all()
+
+
+def test_fp64_free_running_is_close_to_oracle(kn, oracle_mod):
+    """In FP64 the GPU and oracle controllers see the same numbers up to
+    rounding, so most zones take the identical step sequence."""
+    net = chain_network()
+    orc = oracle_mod.Oracle(net)
+    z = constant_zones(net)
+    ref = orc.integrate(z, 0)
+    g = kn.Network(net)
+    g.set_zones(z)
+    kn.integrate_batch([g], kn.Opts(precision=FP64))
+    r = g.get()
+    assert abs(r["steps"][0] - ref["steps"]) <= 0.02 * ref["steps"]
+    assert _rel_err(r["Y"][0], ref["Y"], 1e-10) < 0.5
+
+
+# --------------------------------------------------------------------------
+# batching, mixed sizes, graphs, determinism
+# --------------------------------------------------------------------------
+def test_mixed_sizes_one_launch(kn, oracle_mod):
+    nets = [chain_network(), net150(), net365()]
+    ends = [1e-4, 3e-11, 1e-11]
+    zs = [profile_zones(n, c, t_end=te) for n, c, te in zip(nets, (20, 9, 5), ends)]
+    gs = [kn.Network(n) for n in nets]
+    for g, z in zip(gs, zs):
+        g.set_zones(z)
+    kn.integrate_batch(gs, kn.Opts(precision=FP64))
+    for n, g, z in zip(nets, gs, zs):
+        orc = oracle_mod.Oracle(n)
+        ref = orc.integrate_batch(z, threads=8)
+        r = g.get()
+        assert (r["status"] == 0).all()
+        assert abs(r["steps"].sum() / ref["steps"].sum() - 1) < 0.02
+        for i in range(z.n_zones):
+            assert _rel_err(r["Y"][i], ref["Y"][i], 1e-10) < 0.5
+
+
+def test_graph_and_determinism(kn):
+    net = net150()
+    z = profile_zones(net, 40, t_end=3e-11)
+    g = kn.Network(net)
+    outs = []
+    for use_graph in (0, 1, 1):
+        g.set_zones(z)
+        kn.integrate_batch([g], kn.Opts(precision=MIXED, use_graph=use_graph))
+        outs.append(g.get())
+    for o in outs[1:]:
+        assert np.array_equal(o["Y"], outs[0]["Y"])
+        assert np.array_equal(o["steps"], outs[0]["steps"])
+
+
+def test_device_inputs_and_outputs(kn):
+    import torch
+    net = net150()
+    z = profile_zones(net, 16, t_end=1e-11)
+    g = kn.Network(net)
+    g.set_zones(z)
+    kn.integrate_batch([g], kn.Opts())
+    ref = g.get()
+    dev = torch.device("cuda")
+    dz = {k: torch.from_numpy(np.ascontiguousarray(getattr(z, k))).to(dev)
+          for k in ("Y0", "T0", "rho0", "tau", "t_start", "t_end", "dt_trial")}
+    g.set_zones(dz)
+    kn.integrate_batch([g], kn.Opts())
+    out = {"Y": torch.empty((16, net.n_species), dtype=torch.float64, device=dev),
+           "steps": torch.empty(16, dtype=torch.int64, device=dev)}
+    g.get_device(out)
+    assert np.array_equal(out["Y"].cpu().numpy(), ref["Y"])
+    assert np.array_equal(out["steps"].cpu().numpy(), ref["steps"])
+
+
+# --------------------------------------------------------------------------
+# edge cases and failure statuses (faults are injected on the host)
+# --------------------------------------------------------------------------
+def test_edge_cases(kn, oracle_mod):
+    import torch
+    net = net150()
+    g = kn.Network(net)
+    # invalid host input is refused by the call
+    z = constant_zones(net, 2, t_end=1e-11)
+    z.Y0[1, 3] = np.nan
+    with pytest.raises(kn.KnError):
+        g.set_zones(z)
+    # invalid device input is caught by the integrator: status INVALID, others fine
+    z = constant_zones(net, 3, t_end=1e-11)
+    dz = {k: torch.from_numpy(np.ascontiguousarray(getattr(z, k))).cuda()
+          for k in ("Y0", "T0", "rho0", "tau", "t_start", "t_end", "dt_trial")}
+    dz["Y0"][1, 7] = float("nan")
+    dz["rho0"][2] = -1.0
+    g.set_zones(dz)
+    kn.integrate_batch([g], kn.Opts(precision=FP64))
+    r = g.get()
+    assert r["status"].tolist() == [0, 5, 5]
+    # step limit, max reject, one-step interval
+    z = constant_zones(net, 3, t_end=1e-9)
+    g.set_zones(z)
+    kn.integrate_batch([g], kn.Opts(precision=FP64, max_steps=50))
+    r = g.get()
+    assert (r["status"] == 1).all() and (r["steps"] == 50).all()
+    ref = oracle_mod.Oracle(net).integrate(z, 0, oracle_mod.OracleOpts(max_steps=50))
+    assert _rel_err(r["Y"][0], ref["Y"], 1e-10) < 1e-9
+    kn.integrate_batch([g], kn.Opts(precision=FP64, max_reject=0, grow_max=1e6, safety=1e6))
+    assert (g.get()["status"] == 4).all()
+    z = constant_zones(net, 1, t_end=1e-12 + 1e-15)
+    g.set_zones(z)
+    kn.integrate_batch([g], kn.Opts(precision=FP64))
+    r = g.get()
+    assert r["status"][0] == 0 and r["steps"][0] == 1 and r["t"][0] == z.t_end[0]
+
+
+def test_degenerate_networks(kn, oracle_mod):
+    # a species touched by no reaction, an i -> i reaction, and identical reactants
+    net = custom_network([1, 1, 2, 3], [((0,), (0,)), ((0, 0), (2,)), ((2,), (0, 0))],
+                         [math.log(5.0), math.log(2.0), math.log(1.0)], [0.0, 0.0, 0.0])
+    z = Zones(Y0=np.array([[0.5, 0.2, 0.1, 0.0]]), T0=np.ones(1), rho0=np.ones(1), tau=np.zeros(1),
+              t_start=np.array([1e-3]), t_end=np.array([1.0]), dt_trial=np.array([1e-3]))
+    orc = oracle_mod.Oracle(net)
+    ref = orc.integrate(z, 0, record=10 ** 6)
+    for prec in (FP64, MIXED):
+        r = _replay(kn, net, z, [ref["dts"]], prec)
+        assert r["Y"][0, 1] == 0.2  # untouched species
+        assert _rel_err(r["Y"][0], ref["Y"], 1e-10) < TOL_REPLAY[prec]
+    # a random tiny network through the whole controller
+    net = random_tiny_network(7, 12, 9)
+    z = Zones(Y0=net.initial_Y()[None, :], T0=np.ones(1), rho0=np.ones(1), tau=np.zeros(1),
+              t_start=np.array([0.0]), t_end=np.array([0.5]), dt_trial=np.array([1e-6]))
+    ref = oracle_mod.Oracle(net).integrate(z, 0, record=10 ** 6)
+    r = _replay(kn, net, z, [ref["dts"]], FP64)
+    assert _rel_err(r["Y"][0], ref["Y"], 1e-10) < 1e-9
+
+
+# --------------------------------------------------------------------------
+# full size: the benchmark's 4096-zone 150/1604 batch in its launch
+# configuration, checked on sampled zones and by properties of every zone
+# --------------------------------------------------------------------------
+@pytest.mark.parametrize("prec", [MIXED, FP64])
+def test_full_size_batch_sampled(kn, oracle_mod, prec):
+    net = net150()
+    Z = 4096
+    z = profile_zones(net, Z, t_end=1e-9)
+    g = kn.Network(net)
+    g.set_zones(z)
+    kn.integrate_batch([g], kn.Opts(precision=prec, use_graph=1))
+    r = g.get()
+    assert (r["status"] == 0).all()
+    assert np.array_equal(r["t"], z.t_end)
+    assert (r["Y"] >= 0).all()
+    drift = np.abs((r["Y"] * net.A).sum(1) - 1)
+    assert (drift <= r["steps"] * 1e-6).all()
+    # sampled zones against the oracle: shortest, longest, and spread between
+    order = np.argsort(r["steps"])
+    pick = np.unique(np.concatenate([order[:2], order[-2:], order[:: Z // 8]]))
+    sub = z.subset(pick)
+    ref = oracle_mod.Oracle(net).integrate_batch(sub, threads=16)
+    assert (ref["status"] == 0).all()
+    for a, i in enumerate(pick):
+        assert _rel_err(r["Y"][i], ref["Y"][a], 1e-10) < 10 * 0.05
+    ratio = r["steps"][pick].sum() / ref["steps"].sum()
+    assert abs(ratio - 1) < 0.05, ratio
