@@ -78,7 +78,11 @@ struct Tables {
 struct kn_network {
     int N = 0, R = 0, S_r = 0, S_p = 0;
     std::vector<double> A, lnk0, tn;
-    std::vector<int> reac, prod, nr, slot0;
+    std::vector<int> reac, prod, nr, slot0;  // in the caller's reaction order
+    std::vector<int> perm;                   // sorted position -> caller's reaction index
+    int R1 = 0, R12 = 0;                     // 1-body reactions [0,R1), 2-body [R1,R12)
+    double cmax = 0;
+    DevBuf rate0;                            // double2[R] (ln k0, n), sorted order
     double nbar = 0, rbar = 0;
     std::map<std::pair<int, int>, Tables> tables;  // (precision, Q) -> device blob
     // zone state
@@ -97,16 +101,24 @@ namespace {
 static kn_status build_tables(kn_network* n, int prec, int Q, Tables& T) {
     const int N = n->N, R = n->R;
     const int zero_idx = R + n->S_r;
-    // rows 0..N-1: F+_i (value index j, once per product slot naming i);
+    // sorted order: position jn holds caller reaction perm[jn]; reactant slots
+    // are numbered in sorted order too
+    std::vector<int> sslot0(R);
+    for (int jn = 0, s0 = 0; jn < R; ++jn) {
+        sslot0[jn] = s0;
+        s0 += n->nr[n->perm[jn]];
+    }
+    // rows 0..N-1: F+_i (value index jn, once per product slot naming i);
     // rows N..2N-1: k_i (value index R + reactant slot id naming i)
     std::vector<std::vector<uint16_t>> rows(2 * N);
-    for (int j = 0; j < R; ++j)
+    for (int jn = 0; jn < R; ++jn) {
+        const int j = n->perm[jn];
         for (int q = 0; q < 3; ++q) {
-            int p = n->prod[j * 3 + q];
-            if (p >= 0) rows[p].push_back((uint16_t)j);
+            const int p = n->prod[j * 3 + q];
+            if (p >= 0) rows[p].push_back((uint16_t)jn);
         }
-    for (int j = 0; j < R; ++j)
-        for (int q = 0; q < n->nr[j]; ++q) rows[N + n->reac[j * 3 + q]].push_back((uint16_t)(R + n->slot0[j] + q));
+        for (int q = 0; q < n->nr[j]; ++q) rows[N + n->reac[j * 3 + q]].push_back((uint16_t)(R + sslot0[jn] + q));
+    }
     std::vector<uint16_t> fidx;
     std::vector<int> frow, rstart(2 * N), rend(2 * N);
     for (int r = 0; r < 2 * N; ++r) {
@@ -147,14 +159,15 @@ static kn_status build_tables(kn_network* n, int prec, int Q, Tables& T) {
             fix.push_back(0);
         }
     }
+    const int real = prec == kPrecFP64 ? 8 : 4;
     TableLayout tl{};
     int off = 0;
     tl.off_A = off;
     off = pad16(off + 8 * N);
     tl.off_rspec = off;
     off = pad16(off + 8 * R);
-    tl.off_rate = off;
-    off = pad16(off + 16 * R);
+    tl.off_cexp = off;
+    off = pad16(off + real * R);
     tl.off_terms = off;
     off = pad16(off + 4 * C * Q);
     tl.off_fix = off;
@@ -162,24 +175,20 @@ static kn_status build_tables(kn_network* n, int prec, int Q, Tables& T) {
     tl.bytes = off;
     std::vector<unsigned char> blob(off, 0);
     memcpy(blob.data() + tl.off_A, n->A.data(), 8 * N);
-    for (int j = 0; j < R; ++j) {
+    for (int jn = 0; jn < R; ++jn) {
+        const int j = n->perm[jn];
         uint16_t rs[4];
         rs[0] = (uint16_t)n->reac[j * 3];
         rs[1] = (uint16_t)(n->nr[j] >= 2 ? n->reac[j * 3 + 1] : N);
         rs[2] = (uint16_t)(n->nr[j] >= 3 ? n->reac[j * 3 + 2] : N);
-        rs[3] = (uint16_t)(R + n->slot0[j]);
-        memcpy(blob.data() + tl.off_rspec + 8 * j, rs, 8);
+        rs[3] = (uint16_t)(R + sslot0[jn]);
+        memcpy(blob.data() + tl.off_rspec + 8 * jn, rs, 8);
+        const double c = n->tn[j] + 3.0 * (n->nr[j] - 1);
         if (prec == kPrecFP64) {
-            double p[2] = {n->lnk0[j], n->tn[j]};
-            memcpy(blob.data() + tl.off_rate + 16 * j, p, 16);
+            memcpy(blob.data() + tl.off_cexp + 8 * jn, &c, 8);
         } else {
-            const double a = n->lnk0[j] * 1.4426950408889634;  // log2 units
-            float p[4];
-            p[0] = (float)a;
-            p[1] = (float)(a - (double)p[0]);
-            p[2] = (float)n->tn[j];
-            p[3] = (float)(n->tn[j] - (double)p[2]);
-            memcpy(blob.data() + tl.off_rate + 16 * j, p, 16);
+            const float cf = (float)c;
+            memcpy(blob.data() + tl.off_cexp + 4 * jn, &cf, 4);
         }
     }
     memcpy(blob.data() + tl.off_terms, terms.data(), 4 * terms.size());
@@ -207,24 +216,24 @@ static kn_status get_tables(kn_network* n, int prec, int Q, Tables** out) {
     return KN_OK;
 }
 
-static GroupLayout group_layout(const kn_network* n, int prec, int G, bool has_const) {
+static GroupLayout group_layout(const kn_network* n, int prec, int G, bool /*has_const*/) {
     const int real = prec == kPrecFP64 ? 8 : 4;
     GroupLayout g{};
     int off = 0;
     g.off_V = off;
     off = pad16(off + real * (n->R + n->S_r + 1));
+    g.off_K = off;
+    off = pad16(off + real * n->R);
     g.off_Y64 = off;
     off = pad16(off + 8 * 2 * (n->N + 1));
     g.off_Y32 = off;
     if (prec == kPrecMixed) off = pad16(off + 4 * 2 * (n->N + 1));
     g.off_Fk = off;
-    off = pad16(off + 8 * 2 * n->N);
+    off = pad16(off + real * 2 * n->N);
     g.off_carry = off;
     off = pad16(off + 8 * 2 * G);
-    g.off_kr = off;
-    if (has_const) off = pad16(off + real * n->R);
     g.off_red = off;
-    off = pad16(off + 8 * 4 * 32 + 16);
+    off = pad16(off + 8 * 3 * G + 4 * G);
     g.off_state = off;
     off = pad16(off + (int)sizeof(GroupState));
     g.bytes = off;
@@ -261,9 +270,13 @@ struct Tiling {
     int G = 0, M = 0, smem_tables = 1, bytes = 0;
 };
 
-// Smallest usable zone group for a network: one warp for small networks,
-// a warp group (128 threads) otherwise.
-static int base_group(const kn_network* n) { return n->R + n->S_r + n->S_p <= 512 ? 32 : 128; }
+// Smallest zone group for a network: one warp for small networks; otherwise
+// enough threads (a multiple of 32, at least a warp group) that the FP64
+// update touches every species in a single pass.
+static int base_group(const kn_network* n) {
+    if (n->R + n->S_r + n->S_p <= 512) return 32;
+    return std::max(128, (n->N + 31) / 32 * 32);
+}
 
 // For CTA size P, the tiling of one network: the smallest group size
 // G >= base_group that divides P with at most kMaxGroups groups, preferring
@@ -383,6 +396,24 @@ kn_status kn_create_network(const kn_network_desc* d, kn_network** out) {
     }
     n->S_r = slots;
     n->S_p = pslots;
+    // sort reactions by reactant count (stable): 1-body, then 2-body, then 3-body
+    n->perm.resize(R);
+    for (int j = 0; j < R; ++j) n->perm[j] = j;
+    std::stable_sort(n->perm.begin(), n->perm.end(), [&](int a, int b) { return n->nr[a] < n->nr[b]; });
+    n->R1 = n->R12 = 0;
+    for (int j = 0; j < R; ++j) {
+        n->R1 += n->nr[j] == 1;
+        n->R12 += n->nr[j] <= 2;
+    }
+    std::vector<double> r0(2 * (size_t)R);
+    for (int jn = 0; jn < R; ++jn) {
+        const int j = n->perm[jn];
+        r0[2 * jn] = n->lnk0[j];
+        r0[2 * jn + 1] = n->tn[j];
+        n->cmax = std::max(n->cmax, std::fabs(n->tn[j] + 3.0 * (n->nr[j] - 1)));
+    }
+    KN_CUDA(n->rate0.ensure(16 * (size_t)R));
+    KN_CUDA(cudaMemcpy(n->rate0.p, r0.data(), 16 * (size_t)R, cudaMemcpyHostToDevice));
     if (R + slots + 1 > 65535) return fail(KN_ERR_INVALID_ARG, "network too large for 16-bit gather indices");
     n->nbar = nsum / R;
     n->rbar = rsum / R;
@@ -564,6 +595,10 @@ static kn_status prepare_launch(kn_network* const* nets, int n_nets, const kn_op
         PlanDev& P = lp.plans[p];
         P.blob = (const unsigned char*)tb->blob->p;
         P.tl = tb->tl;
+        P.rate0 = n->rate0.as<const double2>();
+        P.R1 = n->R1;
+        P.R12 = n->R12;
+        P.cmax = n->cmax;
         P.N = n->N;
         P.R = n->R;
         P.S_r = n->S_r;

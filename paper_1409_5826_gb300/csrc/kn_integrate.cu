@@ -45,38 +45,16 @@ __device__ __forceinline__ float ex2_approx(float x) {
     return y;
 }
 
-// Knuth's TwoSum: s + e == a + b exactly.
-__device__ __forceinline__ void two_sum(float a, float b, float& s, float& e) {
-    s = __fadd_rn(a, b);
-    float bb = __fsub_rn(s, a);
-    e = __fadd_rn(__fsub_rn(a, __fsub_rn(s, bb)), __fsub_rn(b, bb));
-}
-
-// Rate k_j = exp(ln k0_j + n_j ln T9 + (r_j - 1) ln rho) evaluated in FP32 as
-// 2^E with E carried as a float pair (hi, lo) in log2 units:
-//   E = a_j + n_j u + (r_j - 1) v,  a_j = ln k0_j / ln 2,  u = ln T9 / ln 2,
-//   v = ln rho / ln 2,
-// then 2^(hi + lo) = 2^hi (1 + lo ln 2) to first order in the tiny lo.
-// Relative error ~ that of ex2.approx (a few ulp), instead of the
-// |E| * 2^-24 a single-float exponent would carry.
-__device__ __forceinline__ float rate_mixed(float4 p, float r1, float u_hi, float u_lo,
-                                            float v_hi, float v_lo) {
-    float ph = __fmul_rn(p.z, u_hi);
-    float pe = __fmaf_rn(p.z, u_hi, -ph);
-    float pl = __fmaf_rn(p.z, u_lo, __fmaf_rn(p.w, u_hi, pe));
-    float qh = __fmul_rn(r1, v_hi);  // r1 in {0, 1, 2}: exact
-    float ql = __fmul_rn(r1, v_lo);
-    float s1, e1, s2, e2;
-    two_sum(p.x, ph, s1, e1);
-    two_sum(s1, qh, s2, e2);
-    float lo = __fadd_rn(__fadd_rn(__fadd_rn(e1, e2), __fadd_rn(p.y, pl)), ql);
-    float hi = __fadd_rn(s2, lo);
-    float lo2 = __fsub_rn(lo, __fsub_rn(hi, s2));
-    return __fmul_rn(ex2_approx(hi), __fmaf_rn(lo2, 0.6931471805599453f, 1.0f));
-}
-
-__device__ __forceinline__ double rate_fp64(double2 p, double r1, double lnT, double lnR) {
-    return exp(fma(p.y, lnT, p.x) + r1 * lnR);
+// exp(-x) for 0 <= x <= 2^-10 by its Taylor series (degree 5: the next term,
+// x^6/720, is below 2^-69 relative), or degree 2 for x <= 1e-6 (x^3/6 below
+// 2^-62).  Written from the series; callers fall back to exp() beyond.
+__device__ __forceinline__ double exp_neg_small(double x, int degree) {
+    if (degree == 2) return fma(x, fma(x, 0.5, -1.0), 1.0);
+    double p = fma(x, -1.0 / 120.0, 1.0 / 24.0);
+    p = fma(x, p, -1.0 / 6.0);
+    p = fma(x, p, 0.5);
+    p = fma(x, p, -1.0);
+    return fma(x, p, 1.0);
 }
 
 // Gather accumulators: plain FP64, or FP32 with Kahan compensation.
@@ -84,10 +62,9 @@ struct AccD {
     double s;
     __device__ __forceinline__ void reset() { s = 0.0; }
     __device__ __forceinline__ void add(double v) { s += v; }
-    __device__ __forceinline__ double get() const { return s; }
 };
 struct AccKahan {
-    float s, c;
+    float s, c;  // sum and (negated) lost low part: value = s - c
     __device__ __forceinline__ void reset() { s = 0.f; c = 0.f; }
     __device__ __forceinline__ void add(float v) {
         float y = __fsub_rn(v, c);
@@ -95,7 +72,6 @@ struct AccKahan {
         c = __fsub_rn(__fsub_rn(t, s), y);
         s = t;
     }
-    __device__ __forceinline__ double get() const { return (double)s - (double)c; }
 };
 
 template <int PREC> struct PrecTraits;
@@ -108,16 +84,11 @@ template <> struct PrecTraits<kPrecMixed> {
     using Acc = AccKahan;
 };
 
-__device__ __forceinline__ void split_double(double x, float& hi, float& lo) {
-    hi = (float)x;
-    lo = (float)(x - (double)hi);
-}
-
 // ---------------------------------------------------------------------------
-// leader-only: set up the next attempt (clipped dt, conditions at t)
+// leader-only: set up the next attempt (clipped dt, profile factor at t)
 // ---------------------------------------------------------------------------
-__device__ __forceinline__ void leader_prepare(GroupState& S, const PlanDev& P, const OptsDev& O,
-                                               float* uv) {
+template <int PREC>
+__device__ __forceinline__ void leader_prepare(GroupState& S, const PlanDev& P, const OptsDev& O) {
     if (S.done) return;
     const int zg = P.zone_base + S.zone;
     if (O.replay_dt) {
@@ -125,7 +96,7 @@ __device__ __forceinline__ void leader_prepare(GroupState& S, const PlanDev& P, 
             S.done = 1;
             return;
         }
-        double h = O.replay_dt[O.replay_off[zg] + S.steps];
+        const double h = O.replay_dt[O.replay_off[zg] + S.steps];
         S.clipped = h >= S.t_end - S.t;
         S.h = h;
     } else {
@@ -138,16 +109,20 @@ __device__ __forceinline__ void leader_prepare(GroupState& S, const PlanDev& P, 
             S.done = 1;
             return;
         }
-        double rem = S.t_end - S.t;
+        const double rem = S.t_end - S.t;
         S.clipped = S.dt >= rem;
         S.h = S.clipped ? rem : S.dt;
     }
     if (!S.rhs_valid && !S.constant) {
-        S.lnT = log(S.T0) - S.t / S.tau;
-        S.lnR = log(S.rho0) - 3.0 * S.t / S.tau;
-        const double l2e = 1.4426950408889634;
-        split_double(S.lnT * l2e, uv[0], uv[1]);
-        split_double(S.lnR * l2e, uv[2], uv[3]);
+        // k_j(t) = K_j exp(-c_j s), s = t / tau: T9 = T0 e^{-s}, rho = rho0 e^{-3s}
+        const double s = S.t * S.inv_tau;
+        S.s = s;
+        if (PREC == kPrecMixed) {
+            S.u = (float)(s * 1.4426950408889634);
+        } else {
+            const double xm = P.cmax * s;
+            S.poly = xm <= 1e-6 ? 2 : (xm <= 0.0009765625 ? 5 : 9);
+        }
     }
 }
 
@@ -160,22 +135,24 @@ __device__ void run_group(const PlanDev& P, const OptsDev& O, const unsigned cha
     using real = typename PrecTraits<PREC>::real;
     using Acc = typename PrecTraits<PREC>::Acc;
     const int N = P.N, R = P.R, G = P.G, Q = P.Q, C = P.C, NP1 = N + 1;
+    const int R1 = P.R1, R12 = P.R12;
 
     const double* __restrict__ A = (const double*)(tb + P.tl.off_A);
     const ushort4* __restrict__ rspec = (const ushort4*)(tb + P.tl.off_rspec);
+    const real* __restrict__ cexp = (const real*)(tb + P.tl.off_cexp);
     const uint32_t* __restrict__ terms = (const uint32_t*)(tb + P.tl.off_terms);
     const ushort4* __restrict__ fix = (const ushort4*)(tb + P.tl.off_fix);
 
     real* V = (real*)(gbase + P.gl.off_V);
+    real* K = (real*)(gbase + P.gl.off_K);
     double* Y64 = (double*)(gbase + P.gl.off_Y64);
     float* Y32 = (float*)(gbase + P.gl.off_Y32);
-    double* Fk = (double*)(gbase + P.gl.off_Fk);
-    double* carry = (double*)(gbase + P.gl.off_carry);
-    real* kr = (real*)(gbase + P.gl.off_kr);
-    double* red = (double*)(gbase + P.gl.off_red);
+    real* Fk = (real*)(gbase + P.gl.off_Fk);
+    double* red_c = (double*)(gbase + P.gl.off_red);  // [G] cons partials
+    double* red_n = red_c + G;                         // [G] ratio numerators
+    double* red_d = red_n + G;                         // [G] ratio denominators
+    int* red_f = (int*)(red_d + G);                    // [G] finite flags
     GroupState& S = *(GroupState*)(gbase + P.gl.off_state);
-    float* uv = (float*)(gbase + P.gl.off_red + 4 * 32 * (int)sizeof(double));  // 4 floats after red
-    const int wid = lane >> 5, nw = G >> 5, wl = lane & 31;
 
     if (lane == 0) V[P.zero_idx] = (real)0;
 
@@ -183,7 +160,7 @@ __device__ void run_group(const PlanDev& P, const OptsDev& O, const unsigned cha
         if (lane == 0) {
             const int q = atomicAdd(P.queue_head, 1);
             S.zone = q < P.n_zones ? P.order[q] : -1;
-            S.finite = 1;  // reused below as "inputs valid"
+            S.valid = 1;
         }
         gs.sync();
         const int z = S.zone;
@@ -215,6 +192,9 @@ __device__ void run_group(const PlanDev& P, const OptsDev& O, const unsigned cha
                 S.t_end = te;
                 S.dt = dtt > 0.0 ? dtt : ts;
                 S.constant = !(tau > 0.0);
+                S.inv_tau = S.constant ? 0.0 : 1.0 / tau;
+                S.poly = 0;
+                S.u = 0.f;
                 S.steps = 0;
                 S.rejects = 0;
                 S.nrej = 0;
@@ -222,42 +202,34 @@ __device__ void run_group(const PlanDev& P, const OptsDev& O, const unsigned cha
                 S.rhs_valid = 0;
                 S.cur = 0;
                 S.done = 0;
-                S.lnT = log(T0);
-                S.lnR = log(rho0);
                 const bool ok = isfinite(T0) && T0 > 0.0 && isfinite(rho0) && rho0 > 0.0 &&
                                 isfinite(tau) && isfinite(ts) && isfinite(te) && ts >= 0.0 &&
                                 te > ts && isfinite(dtt) && (ts > 0.0 || dtt > 0.0);
-                if (!ok) S.finite = 0;
+                if (ok) {
+                    S.lnT0 = log(T0);
+                    S.lnR0 = log(rho0);
+                } else {
+                    S.valid = 0;
+                }
             }
-            if (bad) S.finite = 0;  // benign race: every writer stores 0
+            if (bad) S.valid = 0;  // benign race: every writer stores 0
         }
         gs.sync();
-        if (!S.finite) {
+        if (!S.valid) {
             if (lane == 0) {
                 S.status = 5;  // INVALID
                 S.done = 1;
             }
-        } else if (S.constant) {
-            // rates of a constant-condition zone: once per zone (Sec. 10, note 2)
-            const double lnT = S.lnT, lnR = S.lnR;
+        } else {
+            // the zone's rates at (T0, rho0), once per zone (Sec. 10 item (2))
+            const double lnT0 = S.lnT0, lnR0 = S.lnR0;
             for (int j = lane; j < R; j += G) {
-                const ushort4 rs = rspec[j];
-                const double r1 = (double)((rs.y != N) + (rs.z != N));
-                double k;
-                if (PREC == kPrecFP64) {
-                    k = rate_fp64(((const double2*)(tb + P.tl.off_rate))[j], r1, lnT, lnR);
-                } else {
-                    // FP64 parameters are not staged in mixed mode: rebuild ln k0, n
-                    // from the float pairs (exact to ~2^-48 relative)
-                    const float4 p = ((const float4*)(tb + P.tl.off_rate))[j];
-                    const double a = ((double)p.x + (double)p.y) * 0.6931471805599453;
-                    const double n = (double)p.z + (double)p.w;
-                    k = exp(fma(n, lnT, a) + r1 * lnR);
-                }
-                kr[j] = (real)k;
+                const double2 p = P.rate0[j];
+                const double r1 = (double)((j >= R1) + (j >= R12));
+                K[j] = (real)exp(fma(p.y, lnT0, p.x) + r1 * lnR0);
             }
         }
-        if (lane == 0) leader_prepare(S, P, O, uv);
+        if (lane == 0) leader_prepare<PREC>(S, P, O);
         gs.sync();
 
         // ---- step loop (Sec. 4: adaptive network timesteps) ----
@@ -265,41 +237,63 @@ __device__ void run_group(const PlanDev& P, const OptsDev& O, const unsigned cha
             const int cur = S.cur, nxt = cur ^ 1;
             const double* Yc = Y64 + cur * NP1;
             double* Yn64 = Y64 + nxt * NP1;
-            const float* Yc32 = Y32 + cur * NP1;
-            float* Yn32 = Y32 + nxt * NP1;
 
             if (!S.rhs_valid) {
-                // (a) rates, fluxes f_j and reactant-slot partials (Eq. 1)
-                const bool cst = S.constant;
+                // (a) rates k_j(t), fluxes f_j and reactant-slot partials (Eq. 1),
+                //     reactions sorted 1-, 2-, 3-body: no multiply by a missing reactant
                 if (PREC == kPrecFP64) {
-                    const double lnT = S.lnT, lnR = S.lnR;
-                    const double2* rate = (const double2*)(tb + P.tl.off_rate);
+                    const int poly = S.poly;
+                    const double s = S.s;
                     for (int j = lane; j < R; j += G) {
                         const ushort4 rs = rspec[j];
-                        const double k = cst ? (double)kr[j]
-                                             : rate_fp64(rate[j], (double)((rs.y != N) + (rs.z != N)),
-                                                         lnT, lnR);
-                        const double ya = Yc[rs.x], yb = Yc[rs.y], yc = Yc[rs.z];
-                        const double ka = k * ya;
-                        V[j] = (real)(ka * yb * yc);
-                        V[rs.w] = (real)(k * yb * yc);
-                        if (rs.y != N) V[rs.w + 1] = (real)(ka * yc);
-                        if (rs.z != N) V[rs.w + 2] = (real)(ka * yb);
+                        double k = (double)K[j];
+                        if (poly == 2 || poly == 5)
+                            k *= exp_neg_small((double)cexp[j] * s, poly);
+                        else if (poly == 9)
+                            k *= exp(-(double)cexp[j] * s);
+                        const double ya = Yc[rs.x];
+                        if (j < R1) {
+                            V[j] = (real)(k * ya);
+                            V[rs.w] = (real)k;
+                        } else if (j < R12) {
+                            const double yb = Yc[rs.y];
+                            V[j] = (real)(k * ya * yb);
+                            V[rs.w] = (real)(k * yb);
+                            V[rs.w + 1] = (real)(k * ya);
+                        } else {
+                            const double yb = Yc[rs.y], yc = Yc[rs.z];
+                            const double ka = k * ya;
+                            V[j] = (real)(ka * yb * yc);
+                            V[rs.w] = (real)(k * yb * yc);
+                            V[rs.w + 1] = (real)(ka * yc);
+                            V[rs.w + 2] = (real)(ka * yb);
+                        }
                     }
                 } else {
-                    const float u_hi = uv[0], u_lo = uv[1], v_hi = uv[2], v_lo = uv[3];
-                    const float4* rate = (const float4*)(tb + P.tl.off_rate);
+                    const float* Yc32 = Y32 + cur * NP1;
+                    const float u = S.u;
+                    const bool varying = !S.constant;
                     for (int j = lane; j < R; j += G) {
                         const ushort4 rs = rspec[j];
-                        const float k = cst ? (float)kr[j]
-                                            : rate_mixed(rate[j], (float)((rs.y != N) + (rs.z != N)),
-                                                         u_hi, u_lo, v_hi, v_lo);
-                        const float ya = Yc32[rs.x], yb = Yc32[rs.y], yc = Yc32[rs.z];
-                        const float ka = __fmul_rn(k, ya);
-                        V[j] = (real)__fmul_rn(__fmul_rn(ka, yb), yc);
-                        V[rs.w] = (real)__fmul_rn(__fmul_rn(k, yb), yc);
-                        if (rs.y != N) V[rs.w + 1] = (real)__fmul_rn(ka, yc);
-                        if (rs.z != N) V[rs.w + 2] = (real)__fmul_rn(ka, yb);
+                        float k = (float)K[j];
+                        if (varying) k = __fmul_rn(k, ex2_approx(-__fmul_rn((float)cexp[j], u)));
+                        const float ya = Yc32[rs.x];
+                        if (j < R1) {
+                            V[j] = (real)__fmul_rn(k, ya);
+                            V[rs.w] = (real)k;
+                        } else if (j < R12) {
+                            const float yb = Yc32[rs.y];
+                            V[j] = (real)__fmul_rn(__fmul_rn(k, ya), yb);
+                            V[rs.w] = (real)__fmul_rn(k, yb);
+                            V[rs.w + 1] = (real)__fmul_rn(k, ya);
+                        } else {
+                            const float yb = Yc32[rs.y], yc = Yc32[rs.z];
+                            const float ka = __fmul_rn(k, ya);
+                            V[j] = (real)__fmul_rn(__fmul_rn(ka, yb), yc);
+                            V[rs.w] = (real)__fmul_rn(__fmul_rn(k, yb), yc);
+                            V[rs.w + 1] = (real)__fmul_rn(ka, yc);
+                            V[rs.w + 2] = (real)__fmul_rn(ka, yb);
+                        }
                     }
                 }
                 gs.sync();
@@ -308,28 +302,61 @@ __device__ void run_group(const PlanDev& P, const OptsDev& O, const unsigned cha
                     Acc acc;
                     acc.reset();
                     const uint32_t* tp = terms + lane;
-                    for (int k = 0; k < C; ++k) {
-                        const uint32_t w = tp[k * Q];
-                        acc.add(V[w & 0xffffu]);
-                        if (w & kTermEnd) {
-                            const double val = acc.get();
-                            if (w & kTermHead)
-                                carry[lane] = val;
-                            else
-                                Fk[(w >> kTermRowShift) & kTermRowMask] = val;
-                            acc.reset();
+                    if (PREC == kPrecFP64) {
+                        double* carry = (double*)(gbase + P.gl.off_carry);
+                        for (int k = 0; k < C; ++k) {
+                            const uint32_t w = tp[k * Q];
+                            acc.add((double)V[w & 0xffffu]);
+                            if (w & kTermEnd) {
+                                if (w & kTermHead)
+                                    carry[lane] = (double)acc.s;
+                                else
+                                    Fk[(w >> kTermRowShift) & kTermRowMask] = (real)acc.s;
+                                acc.reset();
+                            }
                         }
+                        carry[Q + lane] = (double)acc.s;
+                    } else {
+                        // FP32 Kahan sums; no FP64 instruction in this loop
+                        AccKahan ak;
+                        ak.reset();
+                        float2* carry = (float2*)(gbase + P.gl.off_carry);
+                        for (int k = 0; k < C; ++k) {
+                            const uint32_t w = tp[k * Q];
+                            ak.add((float)V[w & 0xffffu]);
+                            if (w & kTermEnd) {
+                                if (w & kTermHead)
+                                    carry[lane] = make_float2(ak.s, ak.c);
+                                else
+                                    Fk[(w >> kTermRowShift) & kTermRowMask] = (real)__fsub_rn(ak.s, ak.c);
+                                ak.reset();
+                            }
+                        }
+                        carry[Q + lane] = make_float2(ak.s, ak.c);
                     }
-                    carry[Q + lane] = acc.get();
                 }
                 gs.sync();
                 // (c) rows that cross chunk boundaries: tails of c0..c1-1, head of c1
                 for (int f = lane; f < P.n_fix; f += G) {
                     const ushort4 fx = fix[f];
-                    double s = 0.0;
-                    for (int c = fx.y; c < fx.z; ++c) s += carry[Q + c];
-                    s += carry[fx.z];
-                    Fk[fx.x] = s;
+                    if (PREC == kPrecFP64) {
+                        const double* carry = (const double*)(gbase + P.gl.off_carry);
+                        double s = 0.0;
+                        for (int c = fx.y; c < fx.z; ++c) s += carry[Q + c];
+                        s += carry[fx.z];
+                        Fk[fx.x] = (real)s;
+                    } else {
+                        const float2* carry = (const float2*)(gbase + P.gl.off_carry);
+                        AccKahan ak;
+                        ak.reset();
+                        for (int c = fx.y; c < fx.z; ++c) {
+                            ak.add(carry[Q + c].x);
+                            ak.add(-carry[Q + c].y);
+                        }
+                        ak.add(carry[fx.z].x);
+                        ak.add(-carry[fx.z].y);
+                        Fk[fx.x] = (real)__fsub_rn(ak.s, ak.c);
+                    }
                 }
                 gs.sync();
             }
@@ -339,14 +366,15 @@ __device__ void run_group(const PlanDev& P, const OptsDev& O, const unsigned cha
                 const double h = S.h, kappa = O.kappa, ymin = O.y_min;
                 double csum = 0.0, bn = 0.0, bd = 1.0;
                 int fin = 1;
+                float* Yn32 = Y32 + nxt * NP1;
                 for (int i = lane; i < N; i += G) {
-                    const double y = Yc[i], fp = Fk[i], kk = Fk[N + i];
+                    const double y = Yc[i], fp = (double)Fk[i], kk = (double)Fk[N + i];
                     const double kdt = kk * h;
                     const double yn = (kdt >= kappa) ? (y + h * fp) / (1.0 + kdt) : y + h * (fp - kk * y);
                     Yn64[i] = yn;
                     if (PREC == kPrecMixed) Yn32[i] = (float)yn;
                     const double d = yn - y;
-                    csum += A[i] * d;
+                    csum = fma(A[i], d, csum);
                     const double m = y > yn ? y : yn;
                     if (m > ymin) {
                         const double ad = fabs(d);
@@ -362,9 +390,29 @@ __device__ void run_group(const PlanDev& P, const OptsDev& O, const unsigned cha
                         O.probe_Y1[(size_t)z * N + i] = yn;
                     }
                 }
+                red_c[lane] = csum;
+                red_n[lane] = bn;
+                red_d[lane] = bd;
+                red_f[lane] = fin;
+            }
+            gs.sync();
+
+            // (e) group reduction by warp 0, then accept / reject and the next dt (lane 0)
+            if (lane < 32) {
+                double cs = 0.0, bn = 0.0, bd = 1.0;
+                int fin = 1;
+                for (int q = lane; q < G; q += 32) {
+                    cs += red_c[q];
+                    const double on = red_n[q], od = red_d[q];
+                    if (on * bd > bn * od) {
+                        bn = on;
+                        bd = od;
+                    }
+                    fin &= red_f[q];
+                }
 #pragma unroll
                 for (int off = 16; off > 0; off >>= 1) {
-                    csum += __shfl_xor_sync(0xffffffffu, csum, off);
+                    cs += __shfl_xor_sync(0xffffffffu, cs, off);
                     const double on = __shfl_xor_sync(0xffffffffu, bn, off);
                     const double od = __shfl_xor_sync(0xffffffffu, bd, off);
                     if (on * bd > bn * od) {
@@ -373,65 +421,57 @@ __device__ void run_group(const PlanDev& P, const OptsDev& O, const unsigned cha
                     }
                     fin &= __shfl_xor_sync(0xffffffffu, fin, off);
                 }
-                if (wl == 0) {
-                    red[wid] = csum;
-                    red[32 + wid] = bn;
-                    red[64 + wid] = bd;
-                    red[96 + wid] = (double)fin;
-                }
-            }
-            gs.sync();
-
-            // (e) accept / reject and the next dt (leader)
-            if (lane == 0) {
-                double cs = 0.0, bn = 0.0, bd = 1.0;
-                int fin = 1;
-                for (int w = 0; w < nw; ++w) {
-                    cs += red[w];
-                    const double on = red[32 + w], od = red[64 + w];
-                    if (on * bd > bn * od) {
-                        bn = on;
-                        bd = od;
-                    }
-                    fin &= red[96 + w] != 0.0;
-                }
-                const double cons = fabs(cs);
-                const double rel = bn / bd;
-                const double h = S.h;
-                if (O.probe) {
-                    O.probe_cons[z] = cons;
-                    O.probe_rel[z] = rel;
-                    S.done = 1;
-                } else if (O.replay_dt || (fin && cons <= O.eps_c && rel <= O.eps_r)) {
-                    S.t = S.clipped ? S.t_end : S.t + h;
-                    S.cur = nxt;
-                    S.steps += 1;
-                    S.nrej = 0;
-                    S.rhs_valid = 0;
-                    if (O.replay_dt) {
-                        S.dt = h;
+                if (lane == 0) {
+                    const double cons = fabs(cs);
+                    const double h = S.h;
+                    const bool pass = fin && cons <= O.eps_c && bn <= O.eps_r * bd;
+                    if (O.probe) {
+                        O.probe_cons[z] = cons;
+                        O.probe_rel[z] = bn / bd;
+                        S.done = 1;
+                    } else if (O.replay_dt || pass) {
+                        S.t = S.clipped ? S.t_end : S.t + h;
+                        S.cur = nxt;
+                        S.steps += 1;
+                        S.nrej = 0;
+                        S.rhs_valid = 0;
+                        if (O.replay_dt) {
+                            S.dt = h;
+                        } else if (PREC == kPrecFP64) {
+                            // FP64 form: the proposal in FP64 as well
+                            const double rel = bn / bd;
+                            double gfac = O.grow_max;
+                            const double ga = O.safety * O.eps_r / (rel > 1e-300 ? rel : 1e-300);
+                            const double gb = O.safety * O.eps_c / (cons > 1e-300 ? cons : 1e-300);
+                            if (ga < gfac) gfac = ga;
+                            if (gb < gfac) gfac = gb;
+                            S.dt = h * gfac;
+                        } else {
+                            // mixed form: the accept test above is FP64; the growth
+                            // factor proposal is computed in FP32
+                            const float relf = __fdiv_rn((float)bn, (float)bd);
+                            const float consf = (float)cons;
+                            float gfac = (float)O.grow_max;
+                            const float ga = __fdiv_rn((float)(O.safety * O.eps_r), fmaxf(relf, 1e-30f));
+                            const float gb = __fdiv_rn((float)(O.safety * O.eps_c), fmaxf(consf, 1e-30f));
+                            gfac = fminf(gfac, fminf(ga, gb));
+                            S.dt = h * (double)gfac;
+                        }
                     } else {
-                        double gfac = O.grow_max;
-                        const double ga = O.safety * O.eps_r / (rel > 1e-300 ? rel : 1e-300);
-                        const double gb = O.safety * O.eps_c / (cons > 1e-300 ? cons : 1e-300);
-                        if (ga < gfac) gfac = ga;
-                        if (gb < gfac) gfac = gb;
-                        S.dt = h * gfac;
+                        S.rejects += 1;
+                        S.nrej += 1;
+                        S.rhs_valid = 1;
+                        S.dt = h * O.shrink;
+                        if (S.nrej > O.max_reject) {
+                            S.status = fin ? 4 : 3;  // MAX_REJECT : NONFINITE
+                            S.done = 1;
+                        } else if (S.dt < O.dt_min_frac * S.t) {
+                            S.status = 2;  // DT_UNDERFLOW
+                            S.done = 1;
+                        }
                     }
-                } else {
-                    S.rejects += 1;
-                    S.nrej += 1;
-                    S.rhs_valid = 1;
-                    S.dt = h * O.shrink;
-                    if (S.nrej > O.max_reject) {
-                        S.status = fin ? 4 : 3;  // MAX_REJECT : NONFINITE
-                        S.done = 1;
-                    } else if (S.dt < O.dt_min_frac * S.t) {
-                        S.status = 2;  // DT_UNDERFLOW
-                        S.done = 1;
-                    }
+                    leader_prepare<PREC>(S, P, O);
                 }
-                leader_prepare(S, P, O, uv);
             }
             gs.sync();
         }

@@ -24,13 +24,16 @@ constexpr int kMaxGroups = 15;    // named barriers 1..15
 constexpr int kPrecFP64 = 0;
 constexpr int kPrecMixed = 1;
 
-// One network's tables, as one contiguous device blob per precision; the
-// kernel stages the blob into shared memory when it fits.
+// One network's tables, as one contiguous device blob per (precision, chunk
+// count); the kernel stages the blob into shared memory when it fits.
+// Reactions are stored sorted by reactant count (1-body, 2-body, 3-body) so
+// that the flux loop is warp-uniform and multiplies by no sentinel.
 struct TableLayout {
     int32_t bytes;        // total (multiple of 16)
     int32_t off_A;        // double[N]
     int32_t off_rspec;    // ushort4[R]: reactant species a, b, c (N = none), V index of slot 0
-    int32_t off_rate;     // FP64: double2[R] (ln k0, n); mixed: float4[R] (a_hi, a_lo, n_hi, n_lo), log2 units
+    int32_t off_cexp;     // real[R]: c_j = n_j + 3 (r_j - 1), so that along the profile
+                          //   k_j(t) = k_j(T0, rho0) exp(-c_j t / tau)
     int32_t off_terms;    // uint32[Q * C], chunk-major (term k of chunk c at k*Q + c)
     int32_t off_fix;      // ushort4[n_fix]: (row, first chunk, last chunk, 0)
 };
@@ -38,32 +41,37 @@ struct TableLayout {
 // Per-group shared-memory layout (byte offsets inside one group's region).
 struct GroupLayout {
     int32_t bytes;
-    int32_t off_V;      // real[R + S_r + 1]; last entry is a constant 0
-    int32_t off_Y64;    // double[2][N + 1]; entry N is the constant 1 (product sentinel)
+    int32_t off_V;      // real[R + S_r + 1]: fluxes, reactant-slot partials, constant 0
+    int32_t off_K;      // real[R]: the zone's rates at (T0, rho0)
+    int32_t off_Y64;    // double[2][N + 1]; entry N is the constant 1
     int32_t off_Y32;    // float[2][N + 1] (mixed only)
-    int32_t off_Fk;     // double[2N]: F+ then k
-    int32_t off_carry;  // double[2][Q]: head carries then tail carries
-    int32_t off_kr;     // real[R]: rates of a constant-condition zone
-    int32_t off_red;    // double[4 * 32] reduction scratch
+    int32_t off_Fk;     // real[2N]: F+ then k (mixed: Kahan sums rounded to float)
+    int32_t off_carry;  // FP64: double[2][Q]; mixed: float2[2][Q] Kahan (sum, compensation)
+    int32_t off_red;    // per-lane reduction scratch: double[G] x 3 + int[G]
     int32_t off_state;  // GroupState
 };
 
 struct GroupState {
     double t, dt, t_end, h;
-    double lnT, lnR;          // ln T9, ln rho at the current step start
+    double lnT0, lnR0, inv_tau, s;  // s = t / tau at the current step start
     double T0, rho0, tau;
-    double cons, rel_num, rel_den;
+    double cons, rel;
     long long steps, rejects;
     int zone, status, nrej, rhs_valid;
-    int cur, done, finite, clipped;
-    int constant, accept, pad0, pad1;
+    int cur, done, valid, clipped;
+    int constant, poly, pad0, pad1;  // poly: 0 none (constant), 2/5 Taylor degree, 9 full exp
+    float u;                         // s / ln 2 for the mixed rate factor
+    float pad2[3];
 };
 
 struct PlanDev {
     // tables
     const unsigned char* blob;  // device
     TableLayout tl;
+    const double2* rate0;        // [R] (ln k0_j, n_j), sorted order, global: zone-load rates
     int32_t N, R, S_r, C, Q, n_fix;
+    int32_t R1, R12;             // reactions [0,R1) 1-body, [R1,R12) 2-body, [R12,R) 3-body
+    double cmax;                 // max_j c_j
     int32_t zero_idx;            // V index of the constant zero (= R + S_r)
     int32_t smem_tables;         // 1: stage blob into shared memory
     int32_t G, M;                // threads per zone group, groups per CTA

