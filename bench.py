@@ -39,6 +39,7 @@ def _args():
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--form", default="mixed", choices=["mixed", "fp64"])
     ap.add_argument("--zones", type=int, default=N_ZONES)
+    ap.add_argument("--t-end", type=float, default=T_END, help="integration end time (s)")
     ap.add_argument("--no-cpu", action="store_true", help="skip the CPU baselines")
     ap.add_argument("--tpz", type=int, default=0)
     ap.add_argument("--tpc", type=int, default=0)
@@ -145,7 +146,7 @@ def run_reference(args, rank, world):
     from kn_inputs import net150, profile_zones
     net = net150()
     orc = oracle.Oracle(net)
-    zones = profile_zones(net, args.zones, t_end=T_END)
+    zones = profile_zones(net, args.zones, t_end=args.t_end)
     threads = os.cpu_count() or 1
     pick = np.linspace(0, args.zones - 1, 24).astype(int)
     sub = zones.subset(pick)
@@ -221,7 +222,7 @@ def main():
     build.build()
     net = net150()
     # weak scaling: each rank integrates its own batch of zones (seeds differ by rank)
-    zones = profile_zones(net, args.zones, base_seed=1000 + rank * args.zones, t_end=T_END)
+    zones = profile_zones(net, args.zones, base_seed=1000 + rank * args.zones, t_end=args.t_end)
     dev = torch.device("cuda", local)
     names = ("Y0", "T0", "rho0", "tau", "t_start", "t_end", "dt_trial")
     dz = {k: torch.from_numpy(np.ascontiguousarray(getattr(zones, k))).to(dev) for k in names}
@@ -315,7 +316,9 @@ def main():
             "warmup": max(3, args.warmup), "ms_per_step": ms / args.steps, "higher_is_better": True,
             "scaling": "weak", "vs_baseline": None, "dtype": "f32+f64" if args.form == "mixed" else "f64",
             "data": "synthetic", "zones_per_s": zones_all * args.steps / (ms / 1e3),
-            "config": {"workload": WORKLOAD, "zones_per_gpu": args.zones, "n_species": 150, "n_reactions": 1604,
+            "config": {"workload": WORKLOAD if (args.zones, args.t_end) == (N_ZONES, T_END) else
+                       f"{args.zones} zones x 150sp/1604rx, T9/rho profiles, t 1e-12 -> {args.t_end:g} s",
+                       "zones_per_gpu": args.zones, "n_species": 150, "n_reactions": 1604,
                        "form": args.form, "l2": "flushed between timed steps (256 MB write)",
                        "accepted_steps_per_batch": int(steps_per_batch), "rejects_per_batch": int(st["rejects"]),
                        "zones_ok": int(zones_ok), "parallelism": f"zones sharded, {world} GPU(s)"},
