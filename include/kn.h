@@ -238,6 +238,43 @@ kn_status kn_get_batch_stats(kn_network *const *nets, int32_t n_nets, void *stre
 kn_status kn_probe_step(kn_network *net, const kn_opts *opts, double *Fp, double *k, double *Y1,
                         double *cons, double *rel, void *stream);
 
+/* Largest batch kn_integrate_noalloc accepts (its fixed scratch holds one
+   queue slot per zone: 256 KB of device memory, kept until process exit). */
+#define KN_NOALLOC_MAX_ZONES 65536
+
+/*
+ * kn_integrate_noalloc -- the batched integrator for callers that cannot
+ * allocate GPU memory when they integrate.  The paper has no counterpart:
+ * this is a library convenience.  Typical callers are host simulation codes
+ * that hand out all device memory from their own pre-allocated pool, or whose
+ * per-step path must avoid cudaMalloc/cudaFree (those can synchronise the
+ * device and stall work the code overlaps with the network integration).
+ *
+ * Same integration as kn_integrate_batch for one network, but every zone
+ * array is the caller's (device pointers, row-major as in
+ * kn_zone_conditions / kn_get_abundances): zc holds the inputs; Y [n_zones]
+ * [n_species] receives the abundances at t (Y0 is copied there first), t,
+ * dt_next [n_zones] double, steps, rejects [n_zones] int64, status
+ * [n_zones] int32.  The network's resident tables must already exist for
+ * opts->precision and opts->threads_per_zone (built by any earlier
+ * kn_integrate_batch or kn_probe_step call with those opts, e.g. at set-up);
+ * opts->threads_per_zone must be set (threads_per_cta 0 means one zone group
+ * per CTA); use_graph, replay and mlp must be off.
+ *
+ * Its only scratch (work-queue counter and order) is a fixed device array in
+ * the library, 256 KB per device: no call allocates device memory.  The
+ * first call on each device looks up that array's address; make that first
+ * call before any stream capture.  Every call shares the array and clears
+ * what it needs, so calls whose GPU work overlaps (different streams or
+ * threads) race: serialise them.  Asynchronous on `stream`.
+ * Errors: KN_ERR_INVALID_ARG (NULL pointer, n_zones < 1 or above
+ * KN_NOALLOC_MAX_ZONES, bad opts or tiling), KN_ERR_STATE (tables not built),
+ * KN_ERR_CUDA.
+ */
+kn_status kn_integrate_noalloc(kn_network *net, int32_t n_zones, const kn_zone_conditions *zc,
+                               const kn_opts *opts, double *Y, double *t, double *dt_next,
+                               int64_t *steps, int64_t *rejects, int32_t *status, void *stream);
+
 /* Human-readable description of the most recent failure on this host thread
    (empty string if none).  The pointer stays valid until the next call on
    the same thread. */

@@ -809,3 +809,100 @@ kn_status kn_get_batch_stats(kn_network* const* nets, int32_t n_nets, void* stre
 }
 
 }  // extern "C"
+
+// ---------------------------------------------------------------------------
+// Support for kn_integrate_noalloc (kn_noalloc.cu): fill the launch of one
+// network from tables that already exist, pointing the zone state at the
+// caller's device buffers and the work queue at caller-given scratch.  It
+// builds no tables and allocates nothing; a missing table is an error.
+// ---------------------------------------------------------------------------
+namespace kn {
+kn_status noalloc_prepare(kn_network* n, const kn_opts* o, int32_t n_zones, const kn_zone_conditions* zc,
+                          double* Y_out, double* t_out, double* dt_next, int64_t* steps, int64_t* rejects,
+                          int32_t* status, const int* order, int* queue_head, LaunchParams& lp, int& grid,
+                          int& block, double& nbar, double& rbar) {
+    kn_status s = validate_opts(o);
+    if (s != KN_OK) return s;
+    if (o->use_graph) return fail(KN_ERR_INVALID_ARG, "kn_integrate_noalloc: use_graph must be 0");
+    if (o->replay_dt) return fail(KN_ERR_INVALID_ARG, "kn_integrate_noalloc: replay is not supported");
+    if (o->mlp) return fail(KN_ERR_INVALID_ARG, "kn_integrate_noalloc: learned proposal not supported");
+    const int G = o->threads_per_zone, P = o->threads_per_cta ? o->threads_per_cta : o->threads_per_zone;
+    if (G <= 0) return fail(KN_ERR_INVALID_ARG, "kn_integrate_noalloc: set opts.threads_per_zone (and threads_per_cta)");
+    if (P % G || P / G > kMaxGroups) return fail(KN_ERR_INVALID_ARG, "kn_integrate_noalloc: bad tiling %d/%d", P, G);
+    DeviceInfo di;
+    if ((s = device_info(di)) != KN_OK) return s;
+    auto it = n->tables.find(std::make_pair((int)o->precision, G));
+    if (it == n->tables.end())
+        return fail(KN_ERR_STATE,
+                    "kn_integrate_noalloc: the tables for this precision and threads_per_zone are not built; "
+                    "call kn_integrate_batch or kn_probe_step once with the same opts during set-up");
+    const Tables& tb = it->second;
+    const int budget = di.smem_optin - 1024 - 64;
+    const int M = P / G;
+    const GroupLayout gl = group_layout(n, o->precision, G, true);
+    int smem_tables = tb.tl.bytes + M * gl.bytes <= budget;
+    const int bytes = (smem_tables ? tb.tl.bytes : 0) + M * gl.bytes;
+    if (bytes > budget) return fail(KN_ERR_INVALID_ARG, "kn_integrate_noalloc: tiling needs %d B of shared memory", bytes);
+    memset(&lp, 0, sizeof lp);
+    lp.n_plans = 1;
+    lp.smem_bytes = bytes;
+    PlanDev& Pd = lp.plans[0];
+    Pd.blob = (const unsigned char*)tb.blob->p;
+    Pd.tl = tb.tl;
+    Pd.rate0 = n->rate0.as<const double2>();
+    Pd.R1 = n->R1;
+    Pd.R12 = n->R12;
+    Pd.cmax = n->cmax;
+    Pd.N = n->N;
+    Pd.R = n->R;
+    Pd.S_r = n->S_r;
+    Pd.C = tb.C;
+    Pd.Q = tb.Q;
+    Pd.n_fix = tb.n_fix;
+    Pd.zero_idx = n->R + n->S_r;
+    Pd.smem_tables = smem_tables;
+    Pd.G = G;
+    Pd.M = M;
+    Pd.gl = gl;
+    Pd.Y = Y_out;
+    Pd.T0 = zc->T0;
+    Pd.rho0 = zc->rho0;
+    Pd.tau = zc->tau;
+    Pd.t_start = zc->t_start;
+    Pd.t_end = zc->t_end;
+    Pd.dt_trial = zc->dt_trial;
+    Pd.t_out = t_out;
+    Pd.dt_next = dt_next;
+    Pd.steps = (long long*)steps;
+    Pd.rejects = (long long*)rejects;
+    Pd.status = status;
+    Pd.n_zones = n_zones;
+    Pd.zone_base = 0;
+    Pd.order = order;
+    Pd.queue_head = queue_head;
+    int bps = 0;
+    cudaError_t e = integrator_occupancy(o->precision, P, bytes, &bps);
+    if (e != cudaSuccess) return fail(KN_ERR_CUDA, "occupancy: %s", cudaGetErrorString(e));
+    if (bps < 1) return fail(KN_ERR_INVALID_ARG, "kn_integrate_noalloc: tiling does not fit on an SM");
+    grid = di.sms * bps;
+    block = P;
+    Pd.cta_begin = 0;
+    Pd.cta_end = grid;
+    OptsDev& D = lp.o;
+    D.kappa = o->kappa;
+    D.eps_r = o->eps_r;
+    D.eps_c = o->eps_c;
+    D.y_min = o->y_min;
+    D.grow_max = o->grow_max;
+    D.safety = o->safety;
+    D.shrink = o->shrink;
+    D.dt_min_frac = o->dt_min_frac;
+    D.max_steps = o->max_steps;
+    D.max_reject = o->max_reject;
+    nbar = n->nbar;
+    rbar = n->rbar;
+    return KN_OK;
+}
+
+kn_status noalloc_fail(kn_status s, const char* msg) { return fail(s, "%s", msg); }
+}  // namespace kn

@@ -81,6 +81,7 @@ def lib():
         "kn_get_abundances": (I32, [P, P, P, P, P, P, P, I32, P]),
         "kn_get_batch_stats": (I32, [P, I32, P, C.POINTER(_Stats)]),
         "kn_probe_step": (I32, [P, C.POINTER(_Opts), P, P, P, P, P, P]),
+        "kn_integrate_noalloc": (I32, [P, I32, C.POINTER(_Zones), C.POINTER(_Opts), P, P, P, P, P, P, P]),
     }
     for name, (res, args) in sig.items():
         f = getattr(L, name)
