@@ -233,7 +233,7 @@ static GroupLayout group_layout(const kn_network* n, int prec, int G, bool /*has
     g.off_carry = off;
     off = pad16(off + 8 * 2 * G);
     g.off_red = off;
-    off = pad16(off + 8 * 3 * G + 4 * G);
+    off = pad16(off + 32 * (8 * 3 + 4 + 4));
     g.off_state = off;
     off = pad16(off + (int)sizeof(GroupState));
     g.bytes = off;
@@ -562,6 +562,26 @@ static kn_status prepare_launch(kn_network* const* nets, int n_nets, const kn_op
         int P_lo = 32, P_hi = 1024;
         if (o->threads_per_cta) P_lo = P_hi = o->threads_per_cta;
         else if (o->threads_per_zone) P_lo = P_hi = o->threads_per_zone;
+        if (n_nets == 1 && !o->threads_per_cta) {
+            // one network, no explicit CTA size: the most zone groups per CTA
+            // (tables staged in shared memory), then the smallest group
+            kn_network* n = nets[0];
+            Tiling best;
+            const int g0 = o->threads_per_zone ? o->threads_per_zone : base_group(n);
+            const int g1 = o->threads_per_zone ? o->threads_per_zone : 512;
+            for (int G = g0; G <= g1; G += 32) {
+                Tables* tb;
+                if ((s = get_tables(n, prec, G, &tb)) != KN_OK) return s;
+                const GroupLayout gl = group_layout(n, prec, G, n->has_const);
+                int M = std::min(kMaxGroups, 1024 / G);
+                while (M > 0 && tb->tl.bytes + M * gl.bytes > budget) --M;
+                if (M > best.M) best = Tiling{G, M, 1, tb->tl.bytes + M * gl.bytes};
+            }
+            if (best.M > 0) {
+                P_best = best.G * best.M;
+                tl[0] = best;
+            }
+        }
         // without an explicit tiling: the largest CTA that stages every network's tables
         for (int pass = 0; pass < 2 && !P_best; ++pass) {
             for (int P = P_hi; P >= P_lo && !P_best; P -= 32) {

@@ -148,10 +148,11 @@ __device__ void run_group(const PlanDev& P, const OptsDev& O, const unsigned cha
     double* Y64 = (double*)(gbase + P.gl.off_Y64);
     float* Y32 = (float*)(gbase + P.gl.off_Y32);
     real* Fk = (real*)(gbase + P.gl.off_Fk);
-    double* red_c = (double*)(gbase + P.gl.off_red);  // [G] cons partials
-    double* red_n = red_c + G;                         // [G] ratio numerators
-    double* red_d = red_n + G;                         // [G] ratio denominators
-    int* red_f = (int*)(red_d + G);                    // [G] finite flags
+    double* red_c = (double*)(gbase + P.gl.off_red);  // [32] per-warp cons sums
+    double* red_n = red_c + 32;                        // [32] per-warp ratio numerators (FP64 form)
+    double* red_d = red_n + 32;                        // [32] per-warp ratio denominators
+    float* red_r = (float*)(red_d + 32);               // [32] per-warp max ratio (mixed form)
+    int* red_f = (int*)(red_r + 32);                   // [32] per-warp finite | accept flags
     GroupState& S = *(GroupState*)(gbase + P.gl.off_state);
 
     if (lane == 0) V[P.zero_idx] = (real)0;
@@ -244,93 +245,117 @@ __device__ void run_group(const PlanDev& P, const OptsDev& O, const unsigned cha
                 if (PREC == kPrecFP64) {
                     const int poly = S.poly;
                     const double s = S.s;
+                    const double* __restrict__ Yr = Yc;
+                    const real* __restrict__ Kz = K;
+                    real* __restrict__ Vw = V;
+#pragma unroll 2
                     for (int j = lane; j < R; j += G) {
                         const ushort4 rs = rspec[j];
-                        double k = (double)K[j];
+                        double k = (double)Kz[j];
                         if (poly == 2 || poly == 5)
                             k *= exp_neg_small((double)cexp[j] * s, poly);
                         else if (poly == 9)
                             k *= exp(-(double)cexp[j] * s);
-                        const double ya = Yc[rs.x];
+                        const double ya = Yr[rs.x];
                         if (j < R1) {
-                            V[j] = (real)(k * ya);
-                            V[rs.w] = (real)k;
+                            Vw[j] = (real)(k * ya);
+                            Vw[rs.w] = (real)k;
                         } else if (j < R12) {
-                            const double yb = Yc[rs.y];
-                            V[j] = (real)(k * ya * yb);
-                            V[rs.w] = (real)(k * yb);
-                            V[rs.w + 1] = (real)(k * ya);
+                            const double yb = Yr[rs.y];
+                            Vw[j] = (real)(k * ya * yb);
+                            Vw[rs.w] = (real)(k * yb);
+                            Vw[rs.w + 1] = (real)(k * ya);
                         } else {
-                            const double yb = Yc[rs.y], yc = Yc[rs.z];
+                            const double yb = Yr[rs.y], yc = Yr[rs.z];
                             const double ka = k * ya;
-                            V[j] = (real)(ka * yb * yc);
-                            V[rs.w] = (real)(k * yb * yc);
-                            V[rs.w + 1] = (real)(ka * yc);
-                            V[rs.w + 2] = (real)(ka * yb);
+                            Vw[j] = (real)(ka * yb * yc);
+                            Vw[rs.w] = (real)(k * yb * yc);
+                            Vw[rs.w + 1] = (real)(ka * yc);
+                            Vw[rs.w + 2] = (real)(ka * yb);
                         }
                     }
                 } else {
-                    const float* Yc32 = Y32 + cur * NP1;
+                    const float* __restrict__ Yc32 = Y32 + cur * NP1;
+                    const real* __restrict__ Kz = K;
+                    real* __restrict__ Vw = V;
                     const float u = S.u;
                     const bool varying = !S.constant;
+#pragma unroll 2
                     for (int j = lane; j < R; j += G) {
                         const ushort4 rs = rspec[j];
-                        float k = (float)K[j];
+                        float k = (float)Kz[j];
                         if (varying) k = __fmul_rn(k, ex2_approx(-__fmul_rn((float)cexp[j], u)));
                         const float ya = Yc32[rs.x];
                         if (j < R1) {
-                            V[j] = (real)__fmul_rn(k, ya);
-                            V[rs.w] = (real)k;
+                            Vw[j] = (real)__fmul_rn(k, ya);
+                            Vw[rs.w] = (real)k;
                         } else if (j < R12) {
                             const float yb = Yc32[rs.y];
-                            V[j] = (real)__fmul_rn(__fmul_rn(k, ya), yb);
-                            V[rs.w] = (real)__fmul_rn(k, yb);
-                            V[rs.w + 1] = (real)__fmul_rn(k, ya);
+                            Vw[j] = (real)__fmul_rn(__fmul_rn(k, ya), yb);
+                            Vw[rs.w] = (real)__fmul_rn(k, yb);
+                            Vw[rs.w + 1] = (real)__fmul_rn(k, ya);
                         } else {
                             const float yb = Yc32[rs.y], yc = Yc32[rs.z];
                             const float ka = __fmul_rn(k, ya);
-                            V[j] = (real)__fmul_rn(__fmul_rn(ka, yb), yc);
-                            V[rs.w] = (real)__fmul_rn(__fmul_rn(k, yb), yc);
-                            V[rs.w + 1] = (real)__fmul_rn(ka, yc);
-                            V[rs.w + 2] = (real)__fmul_rn(ka, yb);
+                            Vw[j] = (real)__fmul_rn(__fmul_rn(ka, yb), yc);
+                            Vw[rs.w] = (real)__fmul_rn(__fmul_rn(k, yb), yc);
+                            Vw[rs.w + 1] = (real)__fmul_rn(ka, yc);
+                            Vw[rs.w + 2] = (real)__fmul_rn(ka, yb);
                         }
                     }
                 }
                 gs.sync();
-                // (b) balanced gathers: chunk `lane` of the flat term list
+                // (b) balanced gathers: chunk `lane` of the flat term list; the
+                //     next two terms are loaded ahead of the current one's store
                 if (lane < Q) {
-                    Acc acc;
-                    acc.reset();
-                    const uint32_t* tp = terms + lane;
+                    const uint32_t* __restrict__ tp = terms + lane;
+                    const real* __restrict__ Vr = V;
+                    real* __restrict__ Fw = Fk;
+                    const uint32_t zterm = (uint32_t)P.zero_idx;
+                    uint32_t w0 = tp[0];
+                    uint32_t w1 = C > 1 ? tp[Q] : zterm;
+                    real v0 = Vr[w0 & 0xffffu];
+                    real v1 = Vr[w1 & 0xffffu];
                     if (PREC == kPrecFP64) {
-                        double* carry = (double*)(gbase + P.gl.off_carry);
+                        double* __restrict__ carry = (double*)(gbase + P.gl.off_carry);
+                        double acc = 0.0;
                         for (int k = 0; k < C; ++k) {
-                            const uint32_t w = tp[k * Q];
-                            acc.add((double)V[w & 0xffffu]);
-                            if (w & kTermEnd) {
-                                if (w & kTermHead)
-                                    carry[lane] = (double)acc.s;
+                            const uint32_t w2 = k + 2 < C ? tp[(k + 2) * Q] : zterm;
+                            const real v2 = Vr[w2 & 0xffffu];
+                            acc += (double)v0;
+                            if (w0 & kTermEnd) {
+                                if (w0 & kTermHead)
+                                    carry[lane] = acc;
                                 else
-                                    Fk[(w >> kTermRowShift) & kTermRowMask] = (real)acc.s;
-                                acc.reset();
+                                    Fw[(w0 >> kTermRowShift) & kTermRowMask] = (real)acc;
+                                acc = 0.0;
                             }
+                            w0 = w1;
+                            v0 = v1;
+                            w1 = w2;
+                            v1 = v2;
                         }
-                        carry[Q + lane] = (double)acc.s;
+                        carry[Q + lane] = acc;
                     } else {
                         // FP32 Kahan sums; no FP64 instruction in this loop
+                        float2* __restrict__ carry = (float2*)(gbase + P.gl.off_carry);
                         AccKahan ak;
                         ak.reset();
-                        float2* carry = (float2*)(gbase + P.gl.off_carry);
                         for (int k = 0; k < C; ++k) {
-                            const uint32_t w = tp[k * Q];
-                            ak.add((float)V[w & 0xffffu]);
-                            if (w & kTermEnd) {
-                                if (w & kTermHead)
+                            const uint32_t w2 = k + 2 < C ? tp[(k + 2) * Q] : zterm;
+                            const real v2 = Vr[w2 & 0xffffu];
+                            ak.add((float)v0);
+                            if (w0 & kTermEnd) {
+                                if (w0 & kTermHead)
                                     carry[lane] = make_float2(ak.s, ak.c);
                                 else
-                                    Fk[(w >> kTermRowShift) & kTermRowMask] = (real)__fsub_rn(ak.s, ak.c);
+                                    Fw[(w0 >> kTermRowShift) & kTermRowMask] = (real)__fsub_rn(ak.s, ak.c);
                                 ak.reset();
                             }
+                            w0 = w1;
+                            v0 = v1;
+                            w1 = w2;
+                            v1 = v2;
                         }
                         carry[Q + lane] = make_float2(ak.s, ak.c);
                     }
@@ -361,22 +386,32 @@ __device__ void run_group(const PlanDev& P, const OptsDev& O, const unsigned cha
                 gs.sync();
             }
 
-            // (d) kappa-switched update (Sec. 3, Eq. 3) and error measures, FP64
+            // (d) kappa-switched update (Sec. 3, Eq. 3) and error measures, FP64;
+            //     each warp reduces its own lanes
             {
-                const double h = S.h, kappa = O.kappa, ymin = O.y_min;
+                const double h = S.h, kappa = O.kappa, ymin = O.y_min, eps_r = O.eps_r;
                 double csum = 0.0, bn = 0.0, bd = 1.0;
-                int fin = 1;
+                float rmax = 0.f;
+                int fin = 1, ok = 1;
                 float* Yn32 = Y32 + nxt * NP1;
+                const float* Yc32 = Y32 + cur * NP1;
                 for (int i = lane; i < N; i += G) {
                     const double y = Yc[i], fp = (double)Fk[i], kk = (double)Fk[N + i];
                     const double kdt = kk * h;
                     const double yn = (kdt >= kappa) ? (y + h * fp) / (1.0 + kdt) : y + h * (fp - kk * y);
                     Yn64[i] = yn;
-                    if (PREC == kPrecMixed) Yn32[i] = (float)yn;
                     const double d = yn - y;
                     csum = fma(A[i], d, csum);
                     const double m = y > yn ? y : yn;
-                    if (m > ymin) {
+                    if (PREC == kPrecMixed) {
+                        const float yn32 = (float)yn;
+                        Yn32[i] = yn32;
+                        if (m > ymin) {
+                            ok &= fabs(d) <= eps_r * m ? 1 : 0;  // the accept test, FP64
+                            const float y32 = Yc32[i];           // the dt proposal, FP32
+                            rmax = fmaxf(rmax, __fdividef(fabsf(yn32 - y32), fmaxf(y32, yn32)));
+                        }
+                    } else if (m > ymin) {
                         const double ad = fabs(d);
                         if (ad * bd > bn * m) {
                             bn = ad;
@@ -390,88 +425,101 @@ __device__ void run_group(const PlanDev& P, const OptsDev& O, const unsigned cha
                         O.probe_Y1[(size_t)z * N + i] = yn;
                     }
                 }
-                red_c[lane] = csum;
-                red_n[lane] = bn;
-                red_d[lane] = bd;
-                red_f[lane] = fin;
+#pragma unroll
+                for (int off = 16; off > 0; off >>= 1) {
+                    csum += __shfl_xor_sync(0xffffffffu, csum, off);
+                    if (PREC == kPrecMixed) {
+                        rmax = fmaxf(rmax, __shfl_xor_sync(0xffffffffu, rmax, off));
+                    } else {
+                        const double on = __shfl_xor_sync(0xffffffffu, bn, off);
+                        const double od = __shfl_xor_sync(0xffffffffu, bd, off);
+                        if (on * bd > bn * od) {
+                            bn = on;
+                            bd = od;
+                        }
+                    }
+                }
+                fin = __all_sync(0xffffffffu, fin);
+                ok = __all_sync(0xffffffffu, ok);
+                if ((lane & 31) == 0) {
+                    const int w = lane >> 5;
+                    red_c[w] = csum;
+                    red_n[w] = bn;
+                    red_d[w] = bd;
+                    red_r[w] = rmax;
+                    red_f[w] = fin | (ok << 1);
+                }
             }
             gs.sync();
 
-            // (e) group reduction by warp 0, then accept / reject and the next dt (lane 0)
-            if (lane < 32) {
+            // (e) accept / reject and the next dt (lane 0 combines the warps)
+            if (lane == 0) {
+                const int nw = G >> 5;
                 double cs = 0.0, bn = 0.0, bd = 1.0;
-                int fin = 1;
-                for (int q = lane; q < G; q += 32) {
-                    cs += red_c[q];
-                    const double on = red_n[q], od = red_d[q];
-                    if (on * bd > bn * od) {
-                        bn = on;
-                        bd = od;
-                    }
-                    fin &= red_f[q];
-                }
-#pragma unroll
-                for (int off = 16; off > 0; off >>= 1) {
-                    cs += __shfl_xor_sync(0xffffffffu, cs, off);
-                    const double on = __shfl_xor_sync(0xffffffffu, bn, off);
-                    const double od = __shfl_xor_sync(0xffffffffu, bd, off);
-                    if (on * bd > bn * od) {
-                        bn = on;
-                        bd = od;
-                    }
-                    fin &= __shfl_xor_sync(0xffffffffu, fin, off);
-                }
-                if (lane == 0) {
-                    const double cons = fabs(cs);
-                    const double h = S.h;
-                    const bool pass = fin && cons <= O.eps_c && bn <= O.eps_r * bd;
-                    if (O.probe) {
-                        O.probe_cons[z] = cons;
-                        O.probe_rel[z] = bn / bd;
-                        S.done = 1;
-                    } else if (O.replay_dt || pass) {
-                        S.t = S.clipped ? S.t_end : S.t + h;
-                        S.cur = nxt;
-                        S.steps += 1;
-                        S.nrej = 0;
-                        S.rhs_valid = 0;
-                        if (O.replay_dt) {
-                            S.dt = h;
-                        } else if (PREC == kPrecFP64) {
-                            // FP64 form: the proposal in FP64 as well
-                            const double rel = bn / bd;
-                            double gfac = O.grow_max;
-                            const double ga = O.safety * O.eps_r / (rel > 1e-300 ? rel : 1e-300);
-                            const double gb = O.safety * O.eps_c / (cons > 1e-300 ? cons : 1e-300);
-                            if (ga < gfac) gfac = ga;
-                            if (gb < gfac) gfac = gb;
-                            S.dt = h * gfac;
-                        } else {
-                            // mixed form: the accept test above is FP64; the growth
-                            // factor proposal is computed in FP32
-                            const float relf = __fdiv_rn((float)bn, (float)bd);
-                            const float consf = (float)cons;
-                            float gfac = (float)O.grow_max;
-                            const float ga = __fdiv_rn((float)(O.safety * O.eps_r), fmaxf(relf, 1e-30f));
-                            const float gb = __fdiv_rn((float)(O.safety * O.eps_c), fmaxf(consf, 1e-30f));
-                            gfac = fminf(gfac, fminf(ga, gb));
-                            S.dt = h * (double)gfac;
-                        }
+                float rmax = 0.f;
+                int fin = 1, ok = 1;
+                for (int w = 0; w < nw; ++w) {
+                    cs += red_c[w];
+                    if (PREC == kPrecMixed) {
+                        rmax = fmaxf(rmax, red_r[w]);
                     } else {
-                        S.rejects += 1;
-                        S.nrej += 1;
-                        S.rhs_valid = 1;
-                        S.dt = h * O.shrink;
-                        if (S.nrej > O.max_reject) {
-                            S.status = fin ? 4 : 3;  // MAX_REJECT : NONFINITE
-                            S.done = 1;
-                        } else if (S.dt < O.dt_min_frac * S.t) {
-                            S.status = 2;  // DT_UNDERFLOW
-                            S.done = 1;
+                        const double on = red_n[w], od = red_d[w];
+                        if (on * bd > bn * od) {
+                            bn = on;
+                            bd = od;
                         }
                     }
-                    leader_prepare<PREC>(S, P, O);
+                    fin &= red_f[w] & 1;
+                    ok &= (red_f[w] >> 1) & 1;
                 }
+                const double cons = fabs(cs);
+                const double h = S.h;
+                const bool pass = PREC == kPrecMixed ? (fin && ok && cons <= O.eps_c)
+                                                     : (fin && cons <= O.eps_c && bn <= O.eps_r * bd);
+                if (O.probe) {
+                    O.probe_cons[z] = cons;
+                    O.probe_rel[z] = PREC == kPrecMixed ? (double)rmax : bn / bd;
+                    S.done = 1;
+                } else if (O.replay_dt || pass) {
+                    S.t = S.clipped ? S.t_end : S.t + h;
+                    S.cur = nxt;
+                    S.steps += 1;
+                    S.nrej = 0;
+                    S.rhs_valid = 0;
+                    if (O.replay_dt) {
+                        S.dt = h;
+                    } else if (PREC == kPrecFP64) {
+                        // FP64 form: the proposal in FP64 as well
+                        const double rel = bn / bd;
+                        double gfac = O.grow_max;
+                        const double ga = O.safety * O.eps_r / (rel > 1e-300 ? rel : 1e-300);
+                        const double gb = O.safety * O.eps_c / (cons > 1e-300 ? cons : 1e-300);
+                        if (ga < gfac) gfac = ga;
+                        if (gb < gfac) gfac = gb;
+                        S.dt = h * gfac;
+                    } else {
+                        // mixed form: the accept test above is FP64; the growth
+                        // factor is proposed in FP32
+                        float gfac = (float)O.grow_max;
+                        const float ga = __fdiv_rn((float)(O.safety * O.eps_r), fmaxf(rmax, 1e-30f));
+                        const float gb = __fdiv_rn((float)(O.safety * O.eps_c), fmaxf((float)cons, 1e-30f));
+                        gfac = fminf(gfac, fminf(ga, gb));
+                        S.dt = h * (double)gfac;
+                    }
+                } else {
+                    S.rejects += 1;
+                    S.nrej += 1;
+                    S.rhs_valid = 1;
+                    S.dt = h * O.shrink;
+                    if (S.nrej > O.max_reject) {
+                        S.status = fin ? 4 : 3;  // MAX_REJECT : NONFINITE
+                        S.done = 1;
+                    } else if (S.dt < O.dt_min_frac * S.t) {
+                        S.status = 2;  // DT_UNDERFLOW
+                        S.done = 1;
+                    }
+                }
+                leader_prepare<PREC>(S, P, O);
             }
             gs.sync();
         }

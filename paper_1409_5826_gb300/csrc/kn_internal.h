@@ -47,7 +47,7 @@ struct GroupLayout {
     int32_t off_Y32;    // float[2][N + 1] (mixed only)
     int32_t off_Fk;     // real[2N]: F+ then k (mixed: Kahan sums rounded to float)
     int32_t off_carry;  // FP64: double[2][Q]; mixed: float2[2][Q] Kahan (sum, compensation)
-    int32_t off_red;    // per-lane reduction scratch: double[G] x 3 + int[G]
+    int32_t off_red;    // per-warp reduction scratch: double[32] x 3, float[32], int[32]
     int32_t off_state;  // GroupState
 };
 
