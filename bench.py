@@ -41,6 +41,7 @@ def _args():
     ap.add_argument("--zones", type=int, default=N_ZONES)
     ap.add_argument("--t-end", type=float, default=T_END, help="integration end time (s)")
     ap.add_argument("--no-cpu", action="store_true", help="skip the CPU baselines")
+    ap.add_argument("--no-forms", action="store_true", help="skip the FP64 and learned-dt side measurements")
     ap.add_argument("--tpz", type=int, default=0)
     ap.add_argument("--tpc", type=int, default=0)
     return ap.parse_args()
@@ -196,6 +197,77 @@ def cpu_baselines(net, zones):
     return exp, be
 
 
+def _timed_form(kn, g, dz, stream, opts, reps=2):
+    """One warm-up and `reps` timed batches of a form; returns (ms/batch, stats)."""
+    import torch
+    g.set_zones(dz, stream)
+    kn.integrate_batch([g], opts, stream)
+    torch.cuda.synchronize()
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    ms = 0.0
+    for _ in range(reps):
+        g.set_zones(dz, stream)
+        e0.record(stream)
+        kn.integrate_batch([g], opts, stream)
+        e1.record(stream)
+        torch.cuda.synchronize()
+        ms += e0.elapsed_time(e1)
+    return ms / reps, kn.batch_stats([g], stream)
+
+
+def other_forms(kn, g, net, zones, dz, stream, mixed_steps, mixed_ms):
+    """Side measurements on the same batch: the plain FP64 form and the mixed
+    form with the learned dt proposal (network trained here, untimed, on
+    records the integrator generates from training zones), each with its end-
+    state error against an oracle run at 10x tighter tolerances on 8 zones."""
+    import torch
+    import oracle
+    from kn_inputs import chain_network, profile_zones
+    from paper_1409_5826_gb300 import learned
+    out = {}
+    pick = np.linspace(0, zones.n_zones - 1, 8).astype(int)
+    tight = oracle.Oracle(net).integrate_batch(zones.subset(pick), oracle.OracleOpts(eps_r=0.005, eps_c=1e-7),
+                                               threads=os.cpu_count() or 1)
+
+    def err():
+        Y = g.get(stream)["Y"]
+        e = []
+        for a, i in enumerate(pick):
+            m = tight["Y"][a] > 1e-10
+            e.append(np.median(np.abs(Y[i][m] - tight["Y"][a][m]) / tight["Y"][a][m]))
+        return float(np.median(e))
+
+    ms, st = _timed_form(kn, g, dz, stream, kn.Opts(precision=kn.PREC_MIXED, use_graph=1), reps=1)
+    out["mixed"] = {"ms_per_batch": ms, "zone_steps_per_s": st["steps"] / (ms / 1e3),
+                    "zones_per_s": st["zones_ok"] / (ms / 1e3), "steps": st["steps"], "rejects": st["rejects"],
+                    "median_rel_err_vs_tight_oracle": err()}
+    ms, st = _timed_form(kn, g, dz, stream, kn.Opts(precision=kn.PREC_FP64, use_graph=1), reps=1)
+    out["fp64"] = {"ms_per_batch": ms, "zone_steps_per_s": st["steps"] / (ms / 1e3),
+                   "zones_per_s": st["zones_ok"] / (ms / 1e3), "steps": st["steps"], "rejects": st["rejects"],
+                   "median_rel_err_vs_tight_oracle": err()}
+    t0 = time.perf_counter()
+    jobs = [(net, profile_zones(net, 128, base_seed=500_000, t_end=T_END)),
+            (chain_network(), profile_zones(chain_network(), 32, base_seed=600_000, t_end=1e-2))]
+    feat, lab = learned.generate_records(jobs, 2_000_000, stream=stream)
+    rec_s = time.perf_counter() - t0
+    t0 = time.perf_counter()
+    mlp, hist = learned.train_network(feat, lab, epochs=4, batch=4096, lr=1e-3, stream=stream)
+    torch.cuda.synchronize()
+    train_s = time.perf_counter() - t0
+    ms, st = _timed_form(kn, g, dz, stream, kn.Opts(precision=kn.PREC_MIXED, mlp=mlp, use_graph=1), reps=1)
+    out["mixed_learned"] = {"ms_per_batch": ms, "zone_steps_per_s": st["steps"] / (ms / 1e3),
+                            "zones_per_s": st["zones_ok"] / (ms / 1e3), "steps": st["steps"],
+                            "rejects": st["rejects"], "proposals_used": st["proposals_used"],
+                            "median_rel_err_vs_tight_oracle": err(),
+                            "records": int(feat.shape[0]), "record_gen_s": rec_s, "train_s": train_s,
+                            "train_loss_first_last": [hist[0], hist[-1]]}
+    out["learned_vs_plain_mixed_zones_per_s"] = out["mixed_learned"]["zones_per_s"] / out["mixed"]["zones_per_s"]
+    out["learned_mixed_vs_plain_fp64_zones_per_s"] = out["mixed_learned"]["zones_per_s"] / out["fp64"]["zones_per_s"]
+    out["note"] = "side measurements: 1 warm-up + 1 timed batch each, same 4096-zone batch"
+    mlp.close()
+    return out
+
+
 def main():
     args = _args()
     rank, world, local = _dist()
@@ -323,6 +395,8 @@ def main():
                        "accepted_steps_per_batch": int(steps_per_batch), "rejects_per_batch": int(st["rejects"]),
                        "zones_ok": int(zones_ok), "parallelism": f"zones sharded, {world} GPU(s)"},
             "clocks": clk, "e2e": e2e, "gpu_launches": 3 * args.steps, "roofline": roof}
+    if not args.no_forms:
+        line["forms"] = other_forms(kn, g, net, zones, dz, stream, st["steps"], kms)
     if not args.no_cpu:
         exp, be = cpu_baselines(net, zones)
         line["cpu_baseline"] = exp

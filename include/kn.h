@@ -129,17 +129,33 @@ typedef struct {
     int32_t threads_per_cta;
     int32_t threads_per_zone;
     int32_t use_graph;     /* 1: capture the launch sequence in a CUDA graph and replay it */
-    int32_t lockstep;      /* 1: zone groups of a CTA step together (required by the
-                              learned proposal); 0: independent groups. default 0 */
+    int32_t lockstep;      /* reserved, must be 0 */
     /* Replay (validation): zone z takes exactly replay_len[z] accepted steps
        with dt = replay_dt[replay_off[z] + s], no accept test.  Device pointers;
        zones are numbered across the nets of the call in order. NULL = off. */
     const double *replay_dt;
     const int64_t *replay_off;
     const int64_t *replay_len;
-    /* Learned dt proposal (kn_mlp handle from kn_mlp_create), NULL = off. */
+    /* Learned dt proposal (kn_mlp handle from kn_mlp_create), NULL = off.
+       At every state reached by an accepted step the network proposes
+       dt_mlp = clip(dt_prev e^(out - mlp_margin), dt_plain, 16 dt_plain);
+       the accept test judges it, and a rejected proposal is retried with
+       dt_plain. */
     const void *mlp;
-    int64_t reserved[8];
+    /* Training records for the proposal network: at every state reached by an
+       accepted step, the 64 features and the label ln(dt_best / dt_prev)
+       (dt_best the last step of the grid dt_prev 2^(q/4), q = -8 .. 16, before
+       the first one that fails the accept test from that state; -2 ln 2 if
+       the smallest fails) are appended to these device arrays.
+       *record_count (device, zeroed by the caller) counts every record; those
+       beyond record_capacity are counted but not written.  NULL = off; not
+       combined with mlp. */
+    float *record_features;   /* [record_capacity][64] */
+    float *record_labels;     /* [record_capacity] */
+    int64_t record_capacity;
+    int64_t *record_count;
+    double mlp_margin;        /* ln-units safety margin of the learned proposal, default 0.5 */
+    int64_t reserved[3];
 } kn_opts;
 
 /* Aggregate counters of the last kn_integrate_batch on these networks. */
@@ -237,6 +253,53 @@ kn_status kn_get_batch_stats(kn_network *const *nets, int32_t n_nets, void *stre
  */
 kn_status kn_probe_step(kn_network *net, const kn_opts *opts, double *Fp, double *k, double *Y1,
                         double *cons, double *rel, void *stream);
+
+/* ---------------------------------------------------------------------------
+ * Learned timestep proposal (the paper has no learned component; this is the
+ * library's addition on top of the Sec. 4 controller, which stays the judge
+ * of every step).  A small network maps 64 per-zone features to
+ * ln(dt_next / dt_prev): 64 -> 128 (ReLU) -> 128 (ReLU) -> 1, BF16 weights
+ * and activations, FP32 accumulation, FP32 master weights trained by Adam.
+ * Parameters are one FP32 array of KN_MLP_PARAMS values, in this order:
+ *   W1 [64][128] (input-major), b1 [128], W2 [128][128], b2 [128], w3 [128], b3 [1].
+ * Features are normalised as (f - mu) / sigma before the first layer.
+ * ------------------------------------------------------------------------- */
+#define KN_MLP_FEATURES 64
+#define KN_MLP_HIDDEN 128
+#define KN_MLP_PARAMS 24961
+
+typedef struct kn_mlp kn_mlp; /* opaque: device parameters, Adam state, activations */
+
+/* Create a network with all parameters zero, mu = 0, sigma = 1 (on the
+   current device).  Errors: KN_ERR_INVALID_ARG, KN_ERR_CUDA. */
+kn_status kn_mlp_create(kn_mlp **out);
+
+/* Free the network (after synchronising the device); NULL is ignored. */
+kn_status kn_mlp_destroy(kn_mlp *mlp);
+
+/* Set the FP32 parameters (host array of KN_MLP_PARAMS) and the feature
+   normalisation mu, sigma (host arrays of KN_MLP_FEATURES, sigma > 0); resets
+   the Adam state.  Synchronous.  Errors: KN_ERR_INVALID_ARG, KN_ERR_CUDA. */
+kn_status kn_mlp_set_params(kn_mlp *mlp, const float *params, const float *mu, const float *sigma);
+
+/* Copy the FP32 parameters and the last gradients to host arrays of
+   KN_MLP_PARAMS (either may be NULL).  Synchronises the device. */
+kn_status kn_mlp_get_params(const kn_mlp *mlp, float *params, float *grads);
+
+/* Inference on a batch: features [B][64] and out [B] are device FP32 arrays.
+   Asynchronous on `stream`.  Errors: KN_ERR_INVALID_ARG, KN_ERR_CUDA. */
+kn_status kn_mlp_forward(kn_mlp *mlp, const float *features, int32_t B, float *out, void *stream);
+
+/* Forward and backward pass of the mean squared error against labels [B]
+   (device FP32); the gradients stay in the handle for kn_mlp_adam, and the
+   loss is written to *loss (device FP32 scalar) when loss is not NULL.
+   Asynchronous on `stream`. */
+kn_status kn_mlp_backward(kn_mlp *mlp, const float *features, const float *labels, int32_t B, float *loss,
+                          void *stream);
+
+/* One Adam step on the FP32 master weights with the handle's gradients
+   (bias-corrected, Kingma & Ba), then refresh the BF16 copies.  Asynchronous. */
+kn_status kn_mlp_adam(kn_mlp *mlp, float lr, float beta1, float beta2, float eps, void *stream);
 
 /* Largest batch kn_integrate_noalloc accepts (its fixed scratch holds one
    queue slot per zone: 256 KB of device memory, kept until process exit). */

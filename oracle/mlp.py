@@ -12,9 +12,12 @@ depletion rate k and the previous accepted step dt_prev:
   histogram of their binary exponents: bin = clamp((e + 100) >> 2, 0, 63)
   with e the FP32 exponent (values below 2^-100, and zero, fall in bin 0), the
   quantile linearly interpolated inside its bin, expressed in log10 units.
-Label: ln(dt*/dt_prev), dt* the largest dt_prev * 2^(q/4), q = 16, 15, ..., -8
-  (clipped to t_end - t) whose kappa-switched update passes the accept test
-  from the state; -2 ln 2 if none does.
+Label: ln(dt*/dt_prev), dt* the largest step of the grid dt_prev * 2^(q/4),
+  q = -8, -7, ..., 16 (clipped to t_end - t), below the first grid step whose
+  kappa-switched update fails the accept test from the state; -2 ln 2 if the
+  smallest fails.  (Acceptance is not monotone in dt where the asymptotic
+  update flip-flops, so the largest passing step overall can sit above a
+  failing one; the first failure is what a proposal can learn.)
 MLP: 64 -> 128 (ReLU) -> 128 (ReLU) -> 1 on normalised features
   x = (f - mu) / sigma.  Loss: mean squared error.  Adam (Kingma & Ba 2015).
 
@@ -82,14 +85,19 @@ def features(lnT9: float, lnrho: float, dt_prev: float, Y, Fp, kk, kappa: float 
 
 
 def label(orc, Y, Fp, kk, dt_prev: float, t: float, t_end: float, opts=None) -> float:
-    """ln(dt*/dt_prev) by trying the grid from the largest step down."""
-    for q in range(GRID_HI, GRID_LO - 1, -1):
+    """ln(dt*/dt_prev): walk the grid up from the smallest step and stop at
+    the first failure (or at t_end)."""
+    best = -2.0 * math.log(2.0)
+    for q in range(GRID_LO, GRID_HI + 1):
         h = dt_prev * 2.0 ** (q / 4.0)
         h = min(h, t_end - t)
         Yn, _ = orc.update(Y, Fp, kk, h)
-        if orc.test(Y, Yn, opts)[0]:
-            return math.log(h / dt_prev)
-    return -2.0 * math.log(2.0)
+        if not orc.test(Y, Yn, opts)[0]:
+            break
+        best = math.log(h / dt_prev)
+        if h >= t_end - t:
+            break
+    return best
 
 
 # --------------------------------------------------------------------------

@@ -18,6 +18,10 @@
 
 using namespace kn;
 
+namespace kn {
+void mlp_device_view(const void* h, const float** P, const void** Wb, const float** norm);  // kn_mlp.cu
+}
+
 namespace {
 // ---------------------------------------------------------------------------
 // errors
@@ -87,7 +91,7 @@ struct kn_network {
     std::map<std::pair<int, int>, Tables> tables;  // (precision, Q) -> device blob
     // zone state
     int Z = 0, capZ = 0;
-    DevBuf Y, T0, rho0, tau, ts, te, dtt, tout, dtn, steps, rej, status;
+    DevBuf Y, T0, rho0, tau, ts, te, dtt, tout, dtn, steps, rej, props, status;
     DevBuf key_in, key_out, idx_in, order, cub_tmp, qhead;
     bool has_const = true;  // conservative until zones are known
     bool zones_set = false;
@@ -216,7 +220,7 @@ static kn_status get_tables(kn_network* n, int prec, int Q, Tables** out) {
     return KN_OK;
 }
 
-static GroupLayout group_layout(const kn_network* n, int prec, int G, bool /*has_const*/) {
+static GroupLayout group_layout(const kn_network* n, int prec, int G, bool feat) {
     const int real = prec == kPrecFP64 ? 8 : 4;
     GroupLayout g{};
     int off = 0;
@@ -234,6 +238,8 @@ static GroupLayout group_layout(const kn_network* n, int prec, int G, bool /*has
     off = pad16(off + 8 * 2 * G);
     g.off_red = off;
     off = pad16(off + 32 * (8 * 3 + 4 + 4));
+    g.off_feat = off;
+    if (feat) off = pad16(off + 4 * 384 + 4 * (3 * 64 + 4));
     g.off_state = off;
     off = pad16(off + (int)sizeof(GroupState));
     g.bytes = off;
@@ -281,7 +287,8 @@ static int base_group(const kn_network* n) {
 // For CTA size P, the tiling of one network: the smallest group size
 // G >= base_group that divides P with at most kMaxGroups groups, preferring
 // tables staged in shared memory; bytes = dynamic shared memory per CTA.
-static kn_status plan_tiling(kn_network* n, int prec, int P, int budget, int G_fixed, Tiling& out, bool& ok) {
+static kn_status plan_tiling(kn_network* n, int prec, int P, int budget, int G_fixed, bool feat, Tiling& out,
+                             bool& ok) {
     ok = false;
     Tiling best;
     bool have = false;
@@ -292,7 +299,7 @@ static kn_status plan_tiling(kn_network* n, int prec, int P, int budget, int G_f
         Tables* tb;
         kn_status s = get_tables(n, prec, G, &tb);
         if (s != KN_OK) return s;
-        const GroupLayout gl = group_layout(n, prec, G, n->has_const);
+        const GroupLayout gl = group_layout(n, prec, G, feat);
         if (tb->tl.bytes + M * gl.bytes <= budget) {
             out = Tiling{G, M, 1, tb->tl.bytes + M * gl.bytes};
             ok = true;
@@ -340,6 +347,7 @@ void kn_default_opts(kn_opts* o) {
     o->max_steps = 10000000;
     o->use_graph = 0;
     o->lockstep = 0;
+    o->mlp_margin = 0.5;
 }
 
 const char* kn_last_error(void) { return g_err.c_str(); }
@@ -486,6 +494,7 @@ kn_status kn_set_zone_conditions(kn_network* n, int32_t Z, const kn_zone_conditi
         KN_CUDA(n->dtn.ensure(zd));
         KN_CUDA(n->steps.ensure(zd));
         KN_CUDA(n->rej.ensure(zd));
+        KN_CUDA(n->props.ensure(zd));
         KN_CUDA(n->status.ensure(4 * (size_t)Z));
         KN_CUDA(n->key_in.ensure(4 * (size_t)Z));
         KN_CUDA(n->key_out.ensure(4 * (size_t)Z));
@@ -536,7 +545,11 @@ static kn_status validate_opts(const kn_opts* o) {
         return fail(KN_ERR_INVALID_ARG, "opts.threads_per_zone must be a multiple of 32, <= 1024");
     if (o->threads_per_cta && (o->threads_per_cta % 32 || o->threads_per_cta > 1024))
         return fail(KN_ERR_INVALID_ARG, "opts.threads_per_cta must be a multiple of 32, <= 1024");
-    if (o->lockstep) return fail(KN_ERR_INVALID_ARG, "opts.lockstep is only used with a learned proposal");
+    if (o->lockstep) return fail(KN_ERR_INVALID_ARG, "opts.lockstep is reserved and must be 0");
+    if (o->record_features && (!o->record_labels || !o->record_count || o->record_capacity < 0))
+        return fail(KN_ERR_INVALID_ARG, "opts.record_features needs record_labels, record_count, capacity >= 0");
+    if (o->record_features && o->mlp)
+        return fail(KN_ERR_INVALID_ARG, "opts.record_features and opts.mlp are not combined");
     if ((o->replay_dt != nullptr) != (o->replay_off != nullptr) ||
         (o->replay_dt != nullptr) != (o->replay_len != nullptr))
         return fail(KN_ERR_INVALID_ARG, "opts.replay_dt/off/len must be set together");
@@ -550,7 +563,11 @@ static kn_status prepare_launch(kn_network* const* nets, int n_nets, const kn_op
     kn_status s = device_info(di);
     if (s != KN_OK) return s;
     const int prec = o->precision;
-    const int budget = di.smem_optin - 1024 - 64;
+    const bool learn = o->mlp != nullptr && !probe;
+    const bool record = o->record_features != nullptr && !probe;
+    const bool feat = learn || record;
+    // the staged network takes the front of the CTA's shared memory
+    const int budget = di.smem_optin - 1024 - 64 - (learn ? kMlpSmemBytes : 0);
     memset(&lp, 0, sizeof lp);
     lp.n_plans = n_nets;
     // one CTA size P for the launch; per network the group size G | P
@@ -572,7 +589,7 @@ static kn_status prepare_launch(kn_network* const* nets, int n_nets, const kn_op
             for (int G = g0; G <= g1; G += 32) {
                 Tables* tb;
                 if ((s = get_tables(n, prec, G, &tb)) != KN_OK) return s;
-                const GroupLayout gl = group_layout(n, prec, G, n->has_const);
+                const GroupLayout gl = group_layout(n, prec, G, feat);
                 int M = std::min(kMaxGroups, 1024 / G);
                 while (M > 0 && tb->tl.bytes + M * gl.bytes > budget) --M;
                 if (M > best.M) best = Tiling{G, M, 1, tb->tl.bytes + M * gl.bytes};
@@ -589,7 +606,7 @@ static kn_status prepare_launch(kn_network* const* nets, int n_nets, const kn_op
                 Tiling cand[kMaxPlans];
                 for (int p = 0; p < n_nets && all; ++p) {
                     bool ok;
-                    if ((s = plan_tiling(nets[p], prec, P, budget, o->threads_per_zone, cand[p], ok)) != KN_OK)
+                    if ((s = plan_tiling(nets[p], prec, P, budget, o->threads_per_zone, feat, cand[p], ok)) != KN_OK)
                         return s;
                     all = ok;
                     all_smem = all_smem && ok && cand[p].smem_tables;
@@ -611,7 +628,7 @@ static kn_status prepare_launch(kn_network* const* nets, int n_nets, const kn_op
         const Tiling t = tl[p];
         Tables* tb;
         if ((s = get_tables(n, prec, t.G, &tb)) != KN_OK) return s;
-        const GroupLayout gl = group_layout(n, prec, t.G, n->has_const);
+        const GroupLayout gl = group_layout(n, prec, t.G, feat);
         PlanDev& P = lp.plans[p];
         P.blob = (const unsigned char*)tb->blob->p;
         P.tl = tb->tl;
@@ -641,6 +658,7 @@ static kn_status prepare_launch(kn_network* const* nets, int n_nets, const kn_op
         P.dt_next = n->dtn.as<double>();
         P.steps = n->steps.as<long long>();
         P.rejects = n->rej.as<long long>();
+        P.props = n->props.as<long long>();
         P.status = n->status.as<int>();
         P.n_zones = n->Z;
         P.zone_base = zone_base;
@@ -658,13 +676,14 @@ static kn_status prepare_launch(kn_network* const* nets, int n_nets, const kn_op
         if (lp.plans[p].G * lp.plans[p].M != block)
             return fail(KN_ERR_INVALID_ARG, "networks in one launch need equal threads per CTA (got %d and %d)",
                         lp.plans[p].G * lp.plans[p].M, block);
-    lp.smem_bytes = max_smem;
+    lp.smem_bytes = max_smem + (learn ? kMlpSmemBytes : 0);
     int bps = 0;
     {
-        cudaError_t e = integrator_occupancy(prec, block, max_smem, &bps);
+        cudaError_t e = integrator_occupancy(prec, block, lp.smem_bytes, &bps);
         if (e != cudaSuccess) return fail(KN_ERR_CUDA, "occupancy: %s", cudaGetErrorString(e));
     }
-    if (bps < 1) return fail(KN_ERR_INVALID_ARG, "tiling does not fit on an SM (block %d, smem %d)", block, max_smem);
+    if (bps < 1)
+        return fail(KN_ERR_INVALID_ARG, "tiling does not fit on an SM (block %d, smem %d)", block, lp.smem_bytes);
     grid = di.sms * bps;
     int zones_total = 0;
     for (int p = 0; p < n_nets; ++p) zones_total += lp.plans[p].n_zones;
@@ -693,6 +712,20 @@ static kn_status prepare_launch(kn_network* const* nets, int n_nets, const kn_op
     D.replay_dt = o->replay_dt;
     D.replay_off = (const long long*)o->replay_off;
     D.replay_len = (const long long*)o->replay_len;
+    if (learn) {
+        D.learn = 1;
+        D.mlp_margin = (float)o->mlp_margin;
+        const void* W;
+        mlp_device_view(o->mlp, &D.mlpP, &W, &D.mlpNorm);
+        D.mlpW = W;
+    }
+    if (record) {
+        D.record = 1;
+        D.rec_feat = o->record_features;
+        D.rec_label = o->record_labels;
+        D.rec_cap = o->record_capacity;
+        D.rec_count = (unsigned long long*)o->record_count;
+    }
     return KN_OK;
 }
 
@@ -717,7 +750,6 @@ kn_status kn_integrate_batch(kn_network* const* nets, int32_t n_nets, const kn_o
     }
     kn_status s = validate_opts(o);
     if (s != KN_OK) return s;
-    if (o->mlp) return fail(KN_ERR_INVALID_ARG, "learned proposal not available in this entry point");
     cudaStream_t st = (cudaStream_t)stream_;
     LaunchParams lp;
     int grid, block;
@@ -813,16 +845,18 @@ kn_status kn_get_batch_stats(kn_network* const* nets, int32_t n_nets, void* stre
     for (int p = 0; p < n_nets; ++p) {
         const kn_network* n = nets[p];
         if (!n || !n->zones_set) return fail(KN_ERR_STATE, "network %d has no zones", p);
-        std::vector<int64_t> st(n->Z), rj(n->Z);
+        std::vector<int64_t> st(n->Z), rj(n->Z), pr(n->Z);
         std::vector<int32_t> ss(n->Z);
         kn_status s = kn_get_abundances(n, nullptr, nullptr, nullptr, st.data(), rj.data(), ss.data(),
                                         KN_MEM_HOST, stream_);
         if (s != KN_OK) return s;
+        KN_CUDA(cudaMemcpy(pr.data(), n->props.p, 8 * (size_t)n->Z, cudaMemcpyDeviceToHost));
         for (int z = 0; z < n->Z; ++z) {
             stats->zones += 1;
             stats->zones_ok += ss[z] == KN_ZONE_OK;
             stats->steps += st[z];
             stats->rejects += rj[z];
+            stats->proposals_used += pr[z];
         }
     }
     return KN_OK;
@@ -845,7 +879,8 @@ kn_status noalloc_prepare(kn_network* n, const kn_opts* o, int32_t n_zones, cons
     if (s != KN_OK) return s;
     if (o->use_graph) return fail(KN_ERR_INVALID_ARG, "kn_integrate_noalloc: use_graph must be 0");
     if (o->replay_dt) return fail(KN_ERR_INVALID_ARG, "kn_integrate_noalloc: replay is not supported");
-    if (o->mlp) return fail(KN_ERR_INVALID_ARG, "kn_integrate_noalloc: learned proposal not supported");
+    if (o->mlp || o->record_features)
+        return fail(KN_ERR_INVALID_ARG, "kn_integrate_noalloc: learned proposal and records not supported");
     const int G = o->threads_per_zone, P = o->threads_per_cta ? o->threads_per_cta : o->threads_per_zone;
     if (G <= 0) return fail(KN_ERR_INVALID_ARG, "kn_integrate_noalloc: set opts.threads_per_zone (and threads_per_cta)");
     if (P % G || P / G > kMaxGroups) return fail(KN_ERR_INVALID_ARG, "kn_integrate_noalloc: bad tiling %d/%d", P, G);
@@ -859,7 +894,7 @@ kn_status noalloc_prepare(kn_network* n, const kn_opts* o, int32_t n_zones, cons
     const Tables& tb = it->second;
     const int budget = di.smem_optin - 1024 - 64;
     const int M = P / G;
-    const GroupLayout gl = group_layout(n, o->precision, G, true);
+    const GroupLayout gl = group_layout(n, o->precision, G, false);
     int smem_tables = tb.tl.bytes + M * gl.bytes <= budget;
     const int bytes = (smem_tables ? tb.tl.bytes : 0) + M * gl.bytes;
     if (bytes > budget) return fail(KN_ERR_INVALID_ARG, "kn_integrate_noalloc: tiling needs %d B of shared memory", bytes);

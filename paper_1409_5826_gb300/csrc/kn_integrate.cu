@@ -17,6 +17,8 @@
 //     per-chunk carries), then the kappa-switched FP64 update with
 //     deterministic group reductions for the accept test.
 //   * no spin-waits: every loop is bounded by the zone's step and reject limits.
+#include <cuda_bf16.h>
+
 #include <cstdint>
 
 #include "kn_internal.h"
@@ -129,30 +131,279 @@ __device__ __forceinline__ void leader_prepare(GroupState& S, const PlanDev& P, 
 // ---------------------------------------------------------------------------
 // one zone group: fetch zones until the queue is empty
 // ---------------------------------------------------------------------------
+struct GroupPtrs {
+    const double* A;
+    const ushort4* rspec;
+    const void* cexp;
+    const uint32_t* terms;
+    const ushort4* fix;
+    unsigned char* gbase;
+    void* V;
+    void* K;
+    double* Y64;
+    float* Y32;
+    void* Fk;
+    double* red_c;
+    double* red_n;
+    double* red_d;
+    float* red_r;
+    int* red_f;
+    float* feat;  // [64] features, [64] normalised inputs, [128] h1, [128] h2
+    int* hist;    // [3][64] + [4] counters
+};
+
+// (d) kappa-switched update (Sec. 3, Eq. 3) with step h from buffer cur into
+// nxt, and each warp's share of the error measures (no barrier inside).
 template <int PREC>
-__device__ void run_group(const PlanDev& P, const OptsDev& O, const unsigned char* tb,
+__device__ __forceinline__ void update_reduce(const PlanDev& P, const OptsDev& O, const GroupPtrs& g, int lane,
+                                              int cur, double h, int z) {
+    using real = typename PrecTraits<PREC>::real;
+    const int N = P.N, G = P.G, NP1 = N + 1;
+    const real* Fk = (const real*)g.Fk;
+    const double* Yc = g.Y64 + cur * NP1;
+    double* Yn64 = g.Y64 + (cur ^ 1) * NP1;
+    float* Yn32 = g.Y32 + (cur ^ 1) * NP1;
+    const float* Yc32 = g.Y32 + cur * NP1;
+    const double kappa = O.kappa, ymin = O.y_min, eps_r = O.eps_r;
+    double csum = 0.0, bn = 0.0, bd = 1.0;
+    float rmax = 0.f;
+    int ok = 1;
+    for (int i = lane; i < N; i += G) {
+        const double y = Yc[i], fp = (double)Fk[i], kk = (double)Fk[N + i];
+        const double kdt = kk * h;
+        const double yn = (kdt >= kappa) ? (y + h * fp) / (1.0 + kdt) : y + h * (fp - kk * y);
+        Yn64[i] = yn;
+        const double d = yn - y;
+        csum = fma(g.A[i], d, csum);
+        const double m = y > yn ? y : yn;
+        if (PREC == kPrecMixed) {
+            const float yn32 = (float)yn;
+            Yn32[i] = yn32;
+            if (m > ymin) {
+                ok &= fabs(d) <= eps_r * m ? 1 : 0;  // the accept test, FP64
+                const float y32 = Yc32[i];           // the dt proposal, FP32
+                rmax = fmaxf(rmax, __fdividef(fabsf(yn32 - y32), fmaxf(y32, yn32)));
+            }
+        } else if (m > ymin) {
+            const double ad = fabs(d);
+            if (ad * bd > bn * m) {
+                bn = ad;
+                bd = m;
+            }
+        }
+        if (O.probe) {
+            O.probe_Fp[(size_t)z * N + i] = fp;
+            O.probe_k[(size_t)z * N + i] = kk;
+            O.probe_Y1[(size_t)z * N + i] = yn;
+        }
+    }
+#pragma unroll
+    for (int off = 16; off > 0; off >>= 1) {
+        csum += __shfl_xor_sync(0xffffffffu, csum, off);
+        if (PREC == kPrecMixed) {
+            rmax = fmaxf(rmax, __shfl_xor_sync(0xffffffffu, rmax, off));
+        } else {
+            const double on = __shfl_xor_sync(0xffffffffu, bn, off);
+            const double od = __shfl_xor_sync(0xffffffffu, bd, off);
+            if (on * bd > bn * od) {
+                bn = on;
+                bd = od;
+            }
+        }
+    }
+    ok = __all_sync(0xffffffffu, ok);
+    if ((lane & 31) == 0) {
+        const int w = lane >> 5;
+        g.red_c[w] = csum;
+        g.red_n[w] = bn;
+        g.red_d[w] = bd;
+        g.red_r[w] = rmax;
+        g.red_f[w] = ok;
+    }
+}
+
+// lane 0, after the barrier that follows update_reduce: combine the warps.
+// A non-finite abundance makes the conservation sum non-finite, so the
+// finiteness test reads that sum.
+struct Verdict {
+    double cons, bn, bd;
+    float rmax;
+    int fin, pass;
+};
+template <int PREC>
+__device__ __forceinline__ Verdict combine(const PlanDev& P, const OptsDev& O, const GroupPtrs& g) {
+    const int nw = P.G >> 5;
+    Verdict v{0.0, 0.0, 1.0, 0.f, 1, 0};
+    double cs = 0.0;
+    int ok = 1;
+    for (int w = 0; w < nw; ++w) {
+        cs += g.red_c[w];
+        if (PREC == kPrecMixed) {
+            v.rmax = fmaxf(v.rmax, g.red_r[w]);
+        } else {
+            const double on = g.red_n[w], od = g.red_d[w];
+            if (on * v.bd > v.bn * od) {
+                v.bn = on;
+                v.bd = od;
+            }
+        }
+        ok &= g.red_f[w];
+    }
+    v.fin = isfinite(cs) ? 1 : 0;
+    v.cons = fabs(cs);
+    v.pass = PREC == kPrecMixed ? (v.fin && ok && v.cons <= O.eps_c)
+                                : (v.fin && v.cons <= O.eps_c && v.bn <= O.eps_r * v.bd);
+    return v;
+}
+
+// FP32 exponent histogram bin (4 octaves per bin, values below 2^-100 in bin 0)
+__device__ __forceinline__ int exp_bin(float x) {
+    const unsigned int b = __float_as_uint(x);
+    const int ef = (int)((b >> 23) & 0xffu);
+    if (ef == 0) return 0;  // zero or subnormal
+    const int bin = (ef - 127 + 100) >> 2;
+    return bin < 0 ? 0 : (bin > 63 ? 63 : bin);
+}
+
+__constant__ float kQuantileP[20] = {0.025f, 0.075f, 0.125f, 0.175f, 0.225f, 0.275f, 0.325f,
+                                     0.375f, 0.425f, 0.475f, 0.525f, 0.575f, 0.625f, 0.675f,
+                                     0.725f, 0.775f, 0.825f, 0.875f, 0.925f, 0.975f};
+
+// The 64 features of the current state (group-wide; barriers inside):
+// ln T9, ln rho, ln dt_prev, the fraction of species with k dt_prev >= kappa,
+// and 20 quantiles each of Y, F+ and F- = k Y from FP32 exponent histograms.
+template <int PREC>
+__device__ void compute_features(const PlanDev& P, const OptsDev& O, const GroupPtrs& g, GroupState& S, int lane,
+                                 int cur, const GroupSync& gs) {
+    using real = typename PrecTraits<PREC>::real;
+    const int N = P.N, G = P.G, NP1 = N + 1;
+    const real* Fk = (const real*)g.Fk;
+    for (int i = lane; i < 3 * 64 + 4; i += G) g.hist[i] = 0;
+    gs.sync();
+    const double hp = S.h_prev, kappa = O.kappa;
+    for (int i0 = 0; i0 < N; i0 += G) {
+        const int i = i0 + lane;
+        int asy = 0;
+        if (i < N) {
+            const float y32 = PREC == kPrecMixed ? g.Y32[cur * NP1 + i] : (float)g.Y64[cur * NP1 + i];
+            const float fp = (float)Fk[i], kk = (float)Fk[N + i];
+            atomicAdd(&g.hist[exp_bin(y32)], 1);
+            atomicAdd(&g.hist[64 + exp_bin(fp)], 1);
+            atomicAdd(&g.hist[128 + exp_bin(__fmul_rn(kk, y32))], 1);
+            asy = (double)Fk[N + i] * hp >= kappa;
+        }
+        const unsigned int bal = __ballot_sync(0xffffffffu, asy);
+        if ((lane & 31) == 0 && bal) atomicAdd(&g.hist[192], __popc(bal));
+    }
+    gs.sync();
+    for (int j = lane; j < 61; j += G) {
+        if (j < 60) {
+            const int q = j / 20, m = j - q * 20;
+            const int* h = g.hist + 64 * q;
+            const float target = __fmul_rn(kQuantileP[m], (float)N);
+            int cum = 0;
+            float val = 64.f;
+            for (int b = 0; b < 64; ++b) {
+                const int c = h[b];
+                if (c > 0 && (float)(cum + c) > target) {
+                    val = __fadd_rn((float)b, __fdiv_rn(__fsub_rn(target, (float)cum), (float)c));
+                    break;
+                }
+                cum += c;
+            }
+            g.feat[4 + j] = __fmul_rn(__fsub_rn(__fmul_rn(val, 4.f), 100.f), 0.30102999566398120f);
+        } else {
+            g.feat[0] = (float)(S.lnT0 - S.s);
+            g.feat[1] = (float)(S.lnR0 - 3.0 * S.s);
+            g.feat[2] = logf((float)hp);
+            g.feat[3] = __fdiv_rn((float)g.hist[192], (float)N);
+        }
+    }
+    gs.sync();
+}
+
+// lane 0: append (features, label) to the record buffer
+__device__ __forceinline__ void write_record(const OptsDev& O, const GroupPtrs& g, float label) {
+    const unsigned long long slot = atomicAdd(O.rec_count, 1ull);
+    if ((long long)slot < O.rec_cap) {
+        float* f = O.rec_feat + slot * 64;
+        for (int k = 0; k < 64; ++k) f[k] = g.feat[k];
+        O.rec_label[slot] = label;
+    }
+}
+
+// The network on the group's threads (CUDA cores; one row): BF16 weights
+// staged in shared memory, FP32 accumulation, BF16 activations; returns the
+// network output on lane 0.
+__device__ float mlp_forward_group(const OptsDev& O, const GroupPtrs& g, const unsigned char* mlp_smem, int lane,
+                                   int G, const GroupSync& gs) {
+    const __nv_bfloat16* W1 = (const __nv_bfloat16*)mlp_smem;              // [64][128]
+    const __nv_bfloat16* W2 = W1 + 64 * 128;                                // [128][128]
+    const float* Pb = (const float*)(W2 + 128 * 128);                       // b1 [128], b2 [128], w3 [128], b3
+    const float* nrm = Pb + 3 * 128 + 4;                                    // mu [64], 1/sigma [64]
+    float* x = g.feat + 64;
+    float* h1 = g.feat + 128;
+    float* h2 = g.feat + 256;
+    for (int k = lane; k < 64; k += G) x[k] = __bfloat162float(__float2bfloat16((g.feat[k] - nrm[k]) * nrm[64 + k]));
+    gs.sync();
+    for (int n = lane; n < 128; n += G) {
+        float acc = Pb[n];
+        for (int k = 0; k < 64; ++k) acc = fmaf(x[k], __bfloat162float(W1[k * 128 + n]), acc);
+        h1[n] = __bfloat162float(__float2bfloat16(acc > 0.f ? acc : 0.f));
+    }
+    gs.sync();
+    for (int n = lane; n < 128; n += G) {
+        float acc = Pb[128 + n];
+        for (int k = 0; k < 128; ++k) acc = fmaf(h1[k], __bfloat162float(W2[k * 128 + n]), acc);
+        h2[n] = __bfloat162float(__float2bfloat16(acc > 0.f ? acc : 0.f));
+    }
+    gs.sync();
+    float s = 0.f;
+    if (lane < 32) {
+        for (int n = lane; n < 128; n += 32) s = fmaf(h2[n], Pb[256 + n], s);
+#pragma unroll
+        for (int off = 16; off > 0; off >>= 1) s += __shfl_xor_sync(0xffffffffu, s, off);
+    }
+    return s + Pb[384];
+}
+
+template <int PREC, bool FEAT>
+__device__ void run_group(const PlanDev& P, const OptsDev& O, const unsigned char* tb, const unsigned char* mlp_smem,
                           unsigned char* gbase, const int lane, const GroupSync gs) {
     using real = typename PrecTraits<PREC>::real;
-    using Acc = typename PrecTraits<PREC>::Acc;
     const int N = P.N, R = P.R, G = P.G, Q = P.Q, C = P.C, NP1 = N + 1;
     const int R1 = P.R1, R12 = P.R12;
+    const bool feats_on = FEAT && (O.learn || O.record);
 
-    const double* __restrict__ A = (const double*)(tb + P.tl.off_A);
-    const ushort4* __restrict__ rspec = (const ushort4*)(tb + P.tl.off_rspec);
-    const real* __restrict__ cexp = (const real*)(tb + P.tl.off_cexp);
-    const uint32_t* __restrict__ terms = (const uint32_t*)(tb + P.tl.off_terms);
-    const ushort4* __restrict__ fix = (const ushort4*)(tb + P.tl.off_fix);
+    GroupPtrs g;
+    g.A = (const double*)(tb + P.tl.off_A);
+    g.rspec = (const ushort4*)(tb + P.tl.off_rspec);
+    g.cexp = tb + P.tl.off_cexp;
+    g.terms = (const uint32_t*)(tb + P.tl.off_terms);
+    g.fix = (const ushort4*)(tb + P.tl.off_fix);
+    g.gbase = gbase;
+    g.V = gbase + P.gl.off_V;
+    g.K = gbase + P.gl.off_K;
+    g.Y64 = (double*)(gbase + P.gl.off_Y64);
+    g.Y32 = (float*)(gbase + P.gl.off_Y32);
+    g.Fk = gbase + P.gl.off_Fk;
+    g.red_c = (double*)(gbase + P.gl.off_red);
+    g.red_n = g.red_c + 32;
+    g.red_d = g.red_n + 32;
+    g.red_r = (float*)(g.red_d + 32);
+    g.red_f = (int*)(g.red_r + 32);
+    g.feat = (float*)(gbase + P.gl.off_feat);
+    g.hist = (int*)(g.feat + 384);
 
-    real* V = (real*)(gbase + P.gl.off_V);
-    real* K = (real*)(gbase + P.gl.off_K);
-    double* Y64 = (double*)(gbase + P.gl.off_Y64);
-    float* Y32 = (float*)(gbase + P.gl.off_Y32);
-    real* Fk = (real*)(gbase + P.gl.off_Fk);
-    double* red_c = (double*)(gbase + P.gl.off_red);  // [32] per-warp cons sums
-    double* red_n = red_c + 32;                        // [32] per-warp ratio numerators (FP64 form)
-    double* red_d = red_n + 32;                        // [32] per-warp ratio denominators
-    float* red_r = (float*)(red_d + 32);               // [32] per-warp max ratio (mixed form)
-    int* red_f = (int*)(red_r + 32);                   // [32] per-warp finite | accept flags
+    const ushort4* __restrict__ rspec = g.rspec;
+    const real* __restrict__ cexp = (const real*)g.cexp;
+    const uint32_t* __restrict__ terms = g.terms;
+    const ushort4* __restrict__ fix = g.fix;
+    real* V = (real*)g.V;
+    real* K = (real*)g.K;
+    double* Y64 = g.Y64;
+    float* Y32 = g.Y32;
+    real* Fk = (real*)g.Fk;
     GroupState& S = *(GroupState*)(gbase + P.gl.off_state);
 
     if (lane == 0) V[P.zero_idx] = (real)0;
@@ -194,15 +445,21 @@ __device__ void run_group(const PlanDev& P, const OptsDev& O, const unsigned cha
                 S.dt = dtt > 0.0 ? dtt : ts;
                 S.constant = !(tau > 0.0);
                 S.inv_tau = S.constant ? 0.0 : 1.0 / tau;
+                S.s = 0.0;
                 S.poly = 0;
                 S.u = 0.f;
                 S.steps = 0;
                 S.rejects = 0;
+                S.props = 0;
                 S.nrej = 0;
                 S.status = 0;
                 S.rhs_valid = 0;
                 S.cur = 0;
                 S.done = 0;
+                S.fresh = 0;
+                S.mlp_try = 0;
+                S.h_prev = 0.0;
+                S.dt_plain = 0.0;
                 const bool ok = isfinite(T0) && T0 > 0.0 && isfinite(rho0) && rho0 > 0.0 &&
                                 isfinite(tau) && isfinite(ts) && isfinite(te) && ts >= 0.0 &&
                                 te > ts && isfinite(dtt) && (ts > 0.0 || dtt > 0.0);
@@ -237,7 +494,6 @@ __device__ void run_group(const PlanDev& P, const OptsDev& O, const unsigned cha
         while (!S.done) {
             const int cur = S.cur, nxt = cur ^ 1;
             const double* Yc = Y64 + cur * NP1;
-            double* Yn64 = Y64 + nxt * NP1;
 
             if (!S.rhs_valid) {
                 // (a) rates k_j(t), fluxes f_j and reactant-slot partials (Eq. 1),
@@ -386,114 +642,80 @@ __device__ void run_group(const PlanDev& P, const OptsDev& O, const unsigned cha
                 gs.sync();
             }
 
-            // (d) kappa-switched update (Sec. 3, Eq. 3) and error measures, FP64;
-            //     each warp reduces its own lanes
-            {
-                const double h = S.h, kappa = O.kappa, ymin = O.y_min, eps_r = O.eps_r;
-                double csum = 0.0, bn = 0.0, bd = 1.0;
-                float rmax = 0.f;
-                int fin = 1, ok = 1;
-                float* Yn32 = Y32 + nxt * NP1;
-                const float* Yc32 = Y32 + cur * NP1;
-                for (int i = lane; i < N; i += G) {
-                    const double y = Yc[i], fp = (double)Fk[i], kk = (double)Fk[N + i];
-                    const double kdt = kk * h;
-                    const double yn = (kdt >= kappa) ? (y + h * fp) / (1.0 + kdt) : y + h * (fp - kk * y);
-                    Yn64[i] = yn;
-                    const double d = yn - y;
-                    csum = fma(A[i], d, csum);
-                    const double m = y > yn ? y : yn;
-                    if (PREC == kPrecMixed) {
-                        const float yn32 = (float)yn;
-                        Yn32[i] = yn32;
-                        if (m > ymin) {
-                            ok &= fabs(d) <= eps_r * m ? 1 : 0;  // the accept test, FP64
-                            const float y32 = Yc32[i];           // the dt proposal, FP32
-                            rmax = fmaxf(rmax, __fdividef(fabsf(yn32 - y32), fmaxf(y32, yn32)));
+            // features of a state reached by an accepted step: training records
+            // (label by grid search) or the learned proposal
+            if (FEAT && feats_on && S.fresh) {
+                compute_features<PREC>(P, O, g, S, lane, cur, gs);
+                if (O.record) {
+                    // walk the grid dt_prev 2^(q/4), q = -8 .. 16, up from the
+                    // smallest step; the label is the last step before the first
+                    // failure (or the step that reaches t_end)
+                    float label = -1.3862943611198906f;
+                    for (int q = -8; q <= 16; ++q) {
+                        double hq = S.h_prev * exp2(0.25 * q);
+                        const double rem = S.t_end - S.t;
+                        const bool last = hq >= rem;
+                        if (last) hq = rem;
+                        update_reduce<PREC>(P, O, g, lane, cur, hq, z);
+                        gs.sync();
+                        if (lane == 0) {
+                            const Verdict v = combine<PREC>(P, O, g);
+                            if (v.pass) label = (float)log(hq / S.h_prev);
+                            S.found = !v.pass || last;  // stop
                         }
-                    } else if (m > ymin) {
-                        const double ad = fabs(d);
-                        if (ad * bd > bn * m) {
-                            bn = ad;
-                            bd = m;
-                        }
+                        gs.sync();
+                        if (S.found) break;
                     }
-                    fin &= isfinite(yn) ? 1 : 0;
-                    if (O.probe) {
-                        O.probe_Fp[(size_t)z * N + i] = fp;
-                        O.probe_k[(size_t)z * N + i] = kk;
-                        O.probe_Y1[(size_t)z * N + i] = yn;
-                    }
+                    if (lane == 0) write_record(O, g, label);
                 }
-#pragma unroll
-                for (int off = 16; off > 0; off >>= 1) {
-                    csum += __shfl_xor_sync(0xffffffffu, csum, off);
-                    if (PREC == kPrecMixed) {
-                        rmax = fmaxf(rmax, __shfl_xor_sync(0xffffffffu, rmax, off));
-                    } else {
-                        const double on = __shfl_xor_sync(0xffffffffu, bn, off);
-                        const double od = __shfl_xor_sync(0xffffffffu, bd, off);
-                        if (on * bd > bn * od) {
-                            bn = on;
-                            bd = od;
+                if (O.learn) {
+                    const float out = mlp_forward_group(O, g, mlp_smem, lane, G, gs);
+                    if (lane == 0) {
+                        // dt_mlp = clip(dt_prev e^out, dt_plain, 16 dt_plain), then clipped to t_end
+                        double hm = S.h_prev * (double)expf(fminf(out - O.mlp_margin, 20.f));
+                        const double lo = S.dt_plain, hi = 16.0 * S.dt_plain;
+                        // a proposal at or below the plain step is the plain attempt itself
+                        if (hm > lo) {
+                            hm = hm > hi ? hi : hm;
+                            const double rem = S.t_end - S.t;
+                            S.clipped = hm >= rem;
+                            S.h = S.clipped ? rem : hm;
+                            S.mlp_try = S.h > lo;  // clipping to t_end can leave only the plain step
                         }
                     }
                 }
-                fin = __all_sync(0xffffffffu, fin);
-                ok = __all_sync(0xffffffffu, ok);
-                if ((lane & 31) == 0) {
-                    const int w = lane >> 5;
-                    red_c[w] = csum;
-                    red_n[w] = bn;
-                    red_d[w] = bd;
-                    red_r[w] = rmax;
-                    red_f[w] = fin | (ok << 1);
-                }
+                if (lane == 0) S.fresh = 0;
+                gs.sync();
             }
-            gs.sync();
 
-            // (e) accept / reject and the next dt (lane 0 combines the warps)
+            // (d) update and error measures, then (e) the decision (lane 0)
+            update_reduce<PREC>(P, O, g, lane, cur, S.h, z);
+            gs.sync();
             if (lane == 0) {
-                const int nw = G >> 5;
-                double cs = 0.0, bn = 0.0, bd = 1.0;
-                float rmax = 0.f;
-                int fin = 1, ok = 1;
-                for (int w = 0; w < nw; ++w) {
-                    cs += red_c[w];
-                    if (PREC == kPrecMixed) {
-                        rmax = fmaxf(rmax, red_r[w]);
-                    } else {
-                        const double on = red_n[w], od = red_d[w];
-                        if (on * bd > bn * od) {
-                            bn = on;
-                            bd = od;
-                        }
-                    }
-                    fin &= red_f[w] & 1;
-                    ok &= (red_f[w] >> 1) & 1;
-                }
-                const double cons = fabs(cs);
+                const Verdict v = combine<PREC>(P, O, g);
                 const double h = S.h;
-                const bool pass = PREC == kPrecMixed ? (fin && ok && cons <= O.eps_c)
-                                                     : (fin && cons <= O.eps_c && bn <= O.eps_r * bd);
                 if (O.probe) {
-                    O.probe_cons[z] = cons;
-                    O.probe_rel[z] = PREC == kPrecMixed ? (double)rmax : bn / bd;
+                    O.probe_cons[z] = v.cons;
+                    O.probe_rel[z] = PREC == kPrecMixed ? (double)v.rmax : v.bn / v.bd;
                     S.done = 1;
-                } else if (O.replay_dt || pass) {
+                } else if (O.replay_dt || v.pass) {
                     S.t = S.clipped ? S.t_end : S.t + h;
                     S.cur = nxt;
                     S.steps += 1;
                     S.nrej = 0;
                     S.rhs_valid = 0;
+                    if (S.mlp_try) S.props += 1;
+                    S.mlp_try = 0;
+                    S.h_prev = h;
+                    S.fresh = 1;
                     if (O.replay_dt) {
                         S.dt = h;
                     } else if (PREC == kPrecFP64) {
                         // FP64 form: the proposal in FP64 as well
-                        const double rel = bn / bd;
+                        const double rel = v.bn / v.bd;
                         double gfac = O.grow_max;
                         const double ga = O.safety * O.eps_r / (rel > 1e-300 ? rel : 1e-300);
-                        const double gb = O.safety * O.eps_c / (cons > 1e-300 ? cons : 1e-300);
+                        const double gb = O.safety * O.eps_c / (v.cons > 1e-300 ? v.cons : 1e-300);
                         if (ga < gfac) gfac = ga;
                         if (gb < gfac) gfac = gb;
                         S.dt = h * gfac;
@@ -501,18 +723,25 @@ __device__ void run_group(const PlanDev& P, const OptsDev& O, const unsigned cha
                         // mixed form: the accept test above is FP64; the growth
                         // factor is proposed in FP32
                         float gfac = (float)O.grow_max;
-                        const float ga = __fdiv_rn((float)(O.safety * O.eps_r), fmaxf(rmax, 1e-30f));
-                        const float gb = __fdiv_rn((float)(O.safety * O.eps_c), fmaxf((float)cons, 1e-30f));
+                        const float ga = __fdiv_rn((float)(O.safety * O.eps_r), fmaxf(v.rmax, 1e-30f));
+                        const float gb = __fdiv_rn((float)(O.safety * O.eps_c), fmaxf((float)v.cons, 1e-30f));
                         gfac = fminf(gfac, fminf(ga, gb));
                         S.dt = h * (double)gfac;
                     }
+                    S.dt_plain = S.dt;
+                } else if (S.mlp_try) {
+                    // a rejected learned proposal: retry with the plain controller's dt
+                    S.rejects += 1;
+                    S.rhs_valid = 1;
+                    S.mlp_try = 0;
+                    S.dt = S.dt_plain;
                 } else {
                     S.rejects += 1;
                     S.nrej += 1;
                     S.rhs_valid = 1;
                     S.dt = h * O.shrink;
                     if (S.nrej > O.max_reject) {
-                        S.status = fin ? 4 : 3;  // MAX_REJECT : NONFINITE
+                        S.status = v.fin ? 4 : 3;  // MAX_REJECT : NONFINITE
                         S.done = 1;
                     } else if (S.dt < O.dt_min_frac * S.t) {
                         S.status = 2;  // DT_UNDERFLOW
@@ -535,6 +764,7 @@ __device__ void run_group(const PlanDev& P, const OptsDev& O, const unsigned cha
                 P.dt_next[z] = S.dt;
                 P.steps[z] = S.steps;
                 P.rejects[z] = S.rejects;
+                if (P.props) P.props[z] = S.props;
                 P.status[z] = S.status;
             }
         }
@@ -545,11 +775,31 @@ __device__ void run_group(const PlanDev& P, const OptsDev& O, const unsigned cha
 // ---------------------------------------------------------------------------
 // the persistent kernel
 // ---------------------------------------------------------------------------
-template <int PREC>
+template <int PREC, bool FEAT>
 __global__ void __launch_bounds__(1024, 1) integrate_kernel(const __grid_constant__ LaunchParams lp) {
     extern __shared__ __align__(16) unsigned char smem[];
     __shared__ int s_go;
     const int np = lp.n_plans;
+    // the learned proposal's network, staged once per CTA: BF16 W1, W2, then
+    // FP32 b1, b2, w3, b3 (+3 pad) and mu, 1/sigma
+    const int moff = FEAT && lp.o.learn ? kMlpSmemBytes : 0;
+    if (FEAT && lp.o.learn) {
+        const int4* src = (const int4*)lp.o.mlpW;
+        int4* dst = (int4*)smem;
+        const int nw = (kMlpFeatures * kMlpHidden + kMlpHidden * kMlpHidden) * 2 / 16;
+        for (int i = threadIdx.x; i < nw; i += blockDim.x) dst[i] = src[i];
+        float* Pb = (float*)(smem + nw * 16);
+        const float* P = lp.o.mlpP;
+        const int ob1 = kMlpFeatures * kMlpHidden, ob2 = ob1 + kMlpHidden + kMlpHidden * kMlpHidden,
+                  ow3 = ob2 + kMlpHidden, ob3 = ow3 + kMlpHidden;
+        for (int i = threadIdx.x; i < kMlpHidden; i += blockDim.x) {
+            Pb[i] = P[ob1 + i];
+            Pb[kMlpHidden + i] = P[ob2 + i];
+            Pb[2 * kMlpHidden + i] = P[ow3 + i];
+        }
+        if (threadIdx.x == 0) Pb[3 * kMlpHidden] = P[ob3];
+        for (int i = threadIdx.x; i < 2 * kMlpFeatures; i += blockDim.x) Pb[3 * kMlpHidden + 4 + i] = lp.o.mlpNorm[i];
+    }
     int home = 0;
     for (int p = 0; p < np; ++p)
         if ((int)blockIdx.x >= lp.plans[p].cta_begin && (int)blockIdx.x < lp.plans[p].cta_end) home = p;
@@ -561,19 +811,19 @@ __global__ void __launch_bounds__(1024, 1) integrate_kernel(const __grid_constan
         __syncthreads();
         if (!go) continue;
         const unsigned char* tb = P.blob;
-        int toff = 0;
+        int toff = moff;
         if (P.smem_tables) {
             const int4* src = (const int4*)P.blob;
-            int4* dst = (int4*)smem;
+            int4* dst = (int4*)(smem + moff);
             for (int i = threadIdx.x; i < P.tl.bytes / 16; i += blockDim.x) dst[i] = src[i];
-            tb = smem;
-            toff = P.tl.bytes;
+            tb = smem + moff;
+            toff += P.tl.bytes;
         }
         __syncthreads();
         const int g = threadIdx.x / P.G, lane = threadIdx.x - g * P.G;
         if (g < P.M) {
             GroupSync gs{1 + g, P.G, P.M == 1 && P.G == (int)blockDim.x};
-            run_group<PREC>(P, lp.o, tb, smem + toff + g * P.gl.bytes, lane, gs);
+            run_group<PREC, FEAT>(P, lp.o, tb, smem, smem + toff + g * P.gl.bytes, lane, gs);
         }
         __syncthreads();
     }
@@ -581,27 +831,44 @@ __global__ void __launch_bounds__(1024, 1) integrate_kernel(const __grid_constan
 
 cudaError_t launch_integrator(const LaunchParams& lp, int precision, int grid, int block,
                               cudaStream_t stream) {
-    if (precision == kPrecFP64)
-        integrate_kernel<kPrecFP64><<<grid, block, lp.smem_bytes, stream>>>(lp);
-    else
-        integrate_kernel<kPrecMixed><<<grid, block, lp.smem_bytes, stream>>>(lp);
+    const bool feat = lp.o.learn || lp.o.record;
+    if (precision == kPrecFP64) {
+        if (feat)
+            integrate_kernel<kPrecFP64, true><<<grid, block, lp.smem_bytes, stream>>>(lp);
+        else
+            integrate_kernel<kPrecFP64, false><<<grid, block, lp.smem_bytes, stream>>>(lp);
+    } else {
+        if (feat)
+            integrate_kernel<kPrecMixed, true><<<grid, block, lp.smem_bytes, stream>>>(lp);
+        else
+            integrate_kernel<kPrecMixed, false><<<grid, block, lp.smem_bytes, stream>>>(lp);
+    }
     return cudaGetLastError();
 }
 
 cudaError_t integrator_set_smem_limit(int bytes) {
-    cudaError_t e = cudaFuncSetAttribute(integrate_kernel<kPrecFP64>,
+    cudaError_t e = cudaFuncSetAttribute(integrate_kernel<kPrecFP64, false>,
                                          cudaFuncAttributeMaxDynamicSharedMemorySize, bytes);
-    if (e != cudaSuccess) return e;
-    return cudaFuncSetAttribute(integrate_kernel<kPrecMixed>,
-                                cudaFuncAttributeMaxDynamicSharedMemorySize, bytes);
+    if (e == cudaSuccess)
+        e = cudaFuncSetAttribute(integrate_kernel<kPrecMixed, false>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                 bytes);
+    if (e == cudaSuccess)
+        e = cudaFuncSetAttribute(integrate_kernel<kPrecFP64, true>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                 bytes);
+    if (e == cudaSuccess)
+        e = cudaFuncSetAttribute(integrate_kernel<kPrecMixed, true>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                 bytes);
+    return e;
 }
 
 cudaError_t integrator_occupancy(int precision, int block, int smem, int* blocks_per_sm) {
+    // the FEAT variants use the same shared memory model; occupancy is governed
+    // by shared memory and block size
     if (precision == kPrecFP64)
-        return cudaOccupancyMaxActiveBlocksPerMultiprocessor(blocks_per_sm, integrate_kernel<kPrecFP64>,
+        return cudaOccupancyMaxActiveBlocksPerMultiprocessor(blocks_per_sm, integrate_kernel<kPrecFP64, false>,
                                                              block, smem);
-    return cudaOccupancyMaxActiveBlocksPerMultiprocessor(blocks_per_sm, integrate_kernel<kPrecMixed>,
-                                                         block, smem);
+    return cudaOccupancyMaxActiveBlocksPerMultiprocessor(blocks_per_sm, integrate_kernel<kPrecMixed, false>, block,
+                                                         smem);
 }
 
 // ---------------------------------------------------------------------------

@@ -23,6 +23,13 @@ constexpr int kMaxPlans = 4;      // networks per launch
 constexpr int kMaxGroups = 15;    // named barriers 1..15
 constexpr int kPrecFP64 = 0;
 constexpr int kPrecMixed = 1;
+constexpr int kMlpFeatures = 64;   // learned-proposal network: 64 -> 128 -> 128 -> 1
+constexpr int kMlpHidden = 128;
+constexpr int kMlpParams = kMlpFeatures * kMlpHidden + kMlpHidden + kMlpHidden * kMlpHidden + kMlpHidden +
+                           kMlpHidden + 1;
+// shared memory of the staged network: BF16 W1, W2 + FP32 b1, b2, w3, b3 (+3 pad), mu, 1/sigma
+constexpr int kMlpSmemBytes = (kMlpFeatures * kMlpHidden + kMlpHidden * kMlpHidden) * 2 +
+                              (3 * kMlpHidden + 4 + 2 * kMlpFeatures) * 4;
 
 // One network's tables, as one contiguous device blob per (precision, chunk
 // count); the kernel stages the blob into shared memory when it fits.
@@ -48,6 +55,8 @@ struct GroupLayout {
     int32_t off_Fk;     // real[2N]: F+ then k (mixed: Kahan sums rounded to float)
     int32_t off_carry;  // FP64: double[2][Q]; mixed: float2[2][Q] Kahan (sum, compensation)
     int32_t off_red;    // per-warp reduction scratch: double[32] x 3, float[32], int[32]
+    int32_t off_feat;   // learned proposal / records: float[64 feats, 64 inputs, 128 h1, 128 h2],
+                        //   int[3][64] histograms + 4 counters (absent when unused)
     int32_t off_state;  // GroupState
 };
 
@@ -62,6 +71,14 @@ struct GroupState {
     int constant, poly, pad0, pad1;  // poly: 0 none (constant), 2/5 Taylor degree, 9 full exp
     float u;                         // s / ln 2 for the mixed rate factor
     float pad2[3];
+    // learned proposal / records
+    double h_prev;     // the last accepted step
+    double dt_plain;   // the plain controller's proposal for the current state
+    long long props;   // accepted steps whose dt came from the learned proposal
+    int fresh;         // current state was reached by an accepted step: features due
+    int mlp_try;       // the current attempt uses the learned proposal
+    int found;         // label search: a grid step passed
+    int pad3;
 };
 
 struct PlanDev {
@@ -88,6 +105,7 @@ struct PlanDev {
     double* dt_next;
     long long* steps;
     long long* rejects;
+    long long* props;            // [Z] accepted steps proposed by the network
     int* status;
     int32_t n_zones;
     int32_t zone_base;           // first global zone index of this plan (replay arrays)
@@ -112,6 +130,20 @@ struct OptsDev {
     double* probe_cons;
     double* probe_rel;
     int probe;
+    // records for training the learned proposal: features [cap][64] and labels
+    float* rec_feat;
+    float* rec_label;
+    long long rec_cap;
+    unsigned long long* rec_count;
+    // learned proposal: device parameters of the network (FP32 layout of kn.h),
+    // BF16 W1 [64][128] then W2 [128][128], normalisation mu [64], 1/sigma [64]
+    const float* mlpP;
+    const void* mlpW;
+    const float* mlpNorm;
+    float mlp_margin;  // the proposal uses e^(out - margin)
+    int learn;   // 1: propose with the network
+    int record;  // 1: write (features, label) at every accepted state
+    int mlp_smem_off;  // byte offset of the staged network in the CTA's shared memory
 };
 
 struct LaunchParams {

@@ -49,7 +49,9 @@ class _Opts(C.Structure):
                 ("threads_per_cta", C.c_int32), ("threads_per_zone", C.c_int32),
                 ("use_graph", C.c_int32), ("lockstep", C.c_int32),
                 ("replay_dt", C.c_void_p), ("replay_off", C.c_void_p), ("replay_len", C.c_void_p),
-                ("mlp", C.c_void_p), ("reserved", C.c_int64 * 8)]
+                ("mlp", C.c_void_p), ("record_features", C.c_void_p), ("record_labels", C.c_void_p),
+                ("record_capacity", C.c_int64), ("record_count", C.c_void_p), ("mlp_margin", C.c_double),
+                ("reserved", C.c_int64 * 3)]
 
 
 class _Stats(C.Structure):
@@ -82,6 +84,13 @@ def lib():
         "kn_get_batch_stats": (I32, [P, I32, P, C.POINTER(_Stats)]),
         "kn_probe_step": (I32, [P, C.POINTER(_Opts), P, P, P, P, P, P]),
         "kn_integrate_noalloc": (I32, [P, I32, C.POINTER(_Zones), C.POINTER(_Opts), P, P, P, P, P, P, P]),
+        "kn_mlp_create": (I32, [C.POINTER(P)]),
+        "kn_mlp_destroy": (I32, [P]),
+        "kn_mlp_set_params": (I32, [P, P, P, P]),
+        "kn_mlp_get_params": (I32, [P, P, P]),
+        "kn_mlp_forward": (I32, [P, P, I32, P, P]),
+        "kn_mlp_backward": (I32, [P, P, P, I32, P, P]),
+        "kn_mlp_adam": (I32, [P, C.c_float, C.c_float, C.c_float, C.c_float, P]),
     }
     for name, (res, args) in sig.items():
         f = getattr(L, name)
@@ -131,13 +140,22 @@ class Opts:
     replay_off: int = 0
     replay_len: int = 0
     mlp: int = 0
+    record_features: int = 0
+    record_labels: int = 0
+    record_capacity: int = 0
+    record_count: int = 0
+    mlp_margin: float = 0.5
+
+    _PTRS = ("replay_dt", "replay_off", "replay_len", "mlp", "record_features", "record_labels", "record_count")
 
     def c(self) -> _Opts:
         o = _Opts()
         lib().kn_default_opts(C.byref(o))
         for f in fields(self):
             v = getattr(self, f.name)
-            setattr(o, f.name, (v or None) if f.name in ("replay_dt", "replay_off", "replay_len", "mlp") else v)
+            if f.name == "mlp" and v and not isinstance(v, int):
+                v = v.h.value  # an MLP object
+            setattr(o, f.name, (v or None) if f.name in self._PTRS else v)
         return o
 
 
@@ -246,3 +264,69 @@ def batch_stats(nets, stream=None) -> dict:
     s = _Stats()
     _check(lib().kn_get_batch_stats(arr, len(nets), C.c_void_p(_stream_ptr(stream)), C.byref(s)))
     return {f: getattr(s, f) for f, _ in _Stats._fields_}
+
+
+MLP_FEATURES, MLP_HIDDEN, MLP_PARAMS = 64, 128, 24961
+
+
+def mlp_pack(p: dict) -> np.ndarray:
+    """Flat FP32 parameter array (W1, b1, W2, b2, w3, b3) from a dict of arrays."""
+    return np.concatenate([np.asarray(p[k], np.float64).reshape(-1)
+                           for k in ("W1", "b1", "W2", "b2", "W3", "b3")]).astype(np.float32)
+
+
+def mlp_unpack(flat: np.ndarray) -> dict:
+    F, H = MLP_FEATURES, MLP_HIDDEN
+    o = 0
+    out = {}
+    for k, shape in (("W1", (F, H)), ("b1", (H,)), ("W2", (H, H)), ("b2", (H,)), ("W3", (H, 1)), ("b3", (1,))):
+        n = int(np.prod(shape))
+        out[k] = np.asarray(flat[o:o + n], np.float64).reshape(shape)
+        o += n
+    return out
+
+
+class MLP:
+    """The learned-proposal network on the current device."""
+
+    def __init__(self):
+        h = C.c_void_p()
+        _check(lib().kn_mlp_create(C.byref(h)))
+        self.h = h
+
+    def close(self):
+        if getattr(self, "h", None):
+            lib().kn_mlp_destroy(self.h)
+            self.h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def set_params(self, params: np.ndarray, mu, sigma):
+        params = np.ascontiguousarray(params, np.float32)
+        mu = np.ascontiguousarray(mu, np.float32)
+        sigma = np.ascontiguousarray(sigma, np.float32)
+        assert params.size == MLP_PARAMS and mu.size == MLP_FEATURES and sigma.size == MLP_FEATURES
+        _check(lib().kn_mlp_set_params(self.h, params.ctypes.data, mu.ctypes.data, sigma.ctypes.data))
+
+    def get_params(self):
+        p = np.empty(MLP_PARAMS, np.float32)
+        g = np.empty(MLP_PARAMS, np.float32)
+        _check(lib().kn_mlp_get_params(self.h, p.ctypes.data, g.ctypes.data))
+        return p, g
+
+    def forward(self, feat, out, stream=None):
+        """feat [B, 64] and out [B]: float32 CUDA tensors."""
+        _check(lib().kn_mlp_forward(self.h, feat.data_ptr(), int(feat.shape[0]), out.data_ptr(),
+                                    C.c_void_p(_stream_ptr(stream))))
+
+    def backward(self, feat, labels, loss=None, stream=None):
+        _check(lib().kn_mlp_backward(self.h, feat.data_ptr(), labels.data_ptr(), int(feat.shape[0]),
+                                     loss.data_ptr() if loss is not None else None,
+                                     C.c_void_p(_stream_ptr(stream))))
+
+    def adam(self, lr=1e-3, beta1=0.9, beta2=0.999, eps=1e-8, stream=None):
+        _check(lib().kn_mlp_adam(self.h, lr, beta1, beta2, eps, C.c_void_p(_stream_ptr(stream))))

@@ -123,10 +123,10 @@ def test_features_layout_and_label_property(oracle_mod):
     for q in range(3):
         assert np.all(np.diff(f[4 + 20 * q: 24 + 20 * q]) >= 0)  # quantiles are monotone
     lab = M.label(orc, Y, Fp, kk, dt_prev, t, z.t_end[0])
-    h = dt_prev * math.exp(lab)
-    Yn, _ = orc.update(Y, Fp, kk, h)
-    assert orc.test(Y, Yn)[0]                       # the label's step passes ...
     q = round(lab / math.log(2) * 4)
-    if q < M.GRID_HI:                               # ... and the next grid step up fails
+    for qq in range(M.GRID_LO, q + 1):              # every grid step up to the label passes ...
+        Yn, _ = orc.update(Y, Fp, kk, dt_prev * 2 ** (qq / 4))
+        assert orc.test(Y, Yn)[0]
+    if q < M.GRID_HI:                               # ... and the next one up fails
         Yn, _ = orc.update(Y, Fp, kk, dt_prev * 2 ** ((q + 1) / 4))
         assert not orc.test(Y, Yn)[0]
