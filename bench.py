@@ -241,6 +241,8 @@ def other_forms(kn, g, net, zones, dz, stream, mixed_steps, mixed_ms):
     out["mixed"] = {"ms_per_batch": ms, "zone_steps_per_s": st["steps"] / (ms / 1e3),
                     "zones_per_s": st["zones_ok"] / (ms / 1e3), "steps": st["steps"], "rejects": st["rejects"],
                     "median_rel_err_vs_tight_oracle": err()}
+    g.set_zones(dz, stream)
+    kn.autotune([g], kn.Opts(precision=kn.PREC_FP64), max_steps=100, stream=stream)
     ms, st = _timed_form(kn, g, dz, stream, kn.Opts(precision=kn.PREC_FP64, use_graph=1), reps=1)
     out["fp64"] = {"ms_per_batch": ms, "zone_steps_per_s": st["steps"] / (ms / 1e3),
                    "zones_per_s": st["zones_ok"] / (ms / 1e3), "steps": st["steps"], "rejects": st["rejects"],
@@ -254,6 +256,8 @@ def other_forms(kn, g, net, zones, dz, stream, mixed_steps, mixed_ms):
     mlp, hist = learned.train_network(feat, lab, epochs=4, batch=4096, lr=1e-3, stream=stream)
     torch.cuda.synchronize()
     train_s = time.perf_counter() - t0
+    g.set_zones(dz, stream)
+    kn.autotune([g], kn.Opts(precision=kn.PREC_MIXED, mlp=mlp), max_steps=300, stream=stream)
     ms, st = _timed_form(kn, g, dz, stream, kn.Opts(precision=kn.PREC_MIXED, mlp=mlp, use_graph=1), reps=1)
     out["mixed_learned"] = {"ms_per_batch": ms, "zone_steps_per_s": st["steps"] / (ms / 1e3),
                             "zones_per_s": st["zones_ok"] / (ms / 1e3), "steps": st["steps"],
@@ -300,8 +304,13 @@ def main():
     dz = {k: torch.from_numpy(np.ascontiguousarray(getattr(zones, k))).to(dev) for k in names}
     g = kn.Network(net)
     prec = kn.PREC_MIXED if args.form == "mixed" else kn.PREC_FP64
-    opts = kn.Opts(precision=prec, use_graph=1, threads_per_zone=args.tpz, threads_per_cta=args.tpc)
     stream = torch.cuda.current_stream()
+    tuned = None
+    if not (args.tpz or args.tpc):
+        # the project's autotuner picks the tiling on this batch (untimed set-up)
+        g.set_zones(dz, stream)
+        tuned = kn.autotune([g], kn.Opts(precision=prec), max_steps=300, stream=stream)
+    opts = kn.Opts(precision=prec, use_graph=1, threads_per_zone=args.tpz, threads_per_cta=args.tpc)
     flush = torch.empty(256 * 1024 * 1024 // 4, dtype=torch.float32, device=dev)  # > L2 (129 MB)
 
     def step():
@@ -377,12 +386,20 @@ def main():
     f64, f32 = algorithmic_flops(net, st["steps"], st["rejects"], args.form)
     kms = float(np.mean(kern_ms))
     peaks, src = _peaks()
-    fp64_peak_tf = 1.25  # nominal GB300 FP64 (recipe table); no measured FP64 peak in the peaks file
+    # FP64 bound: the peak is the device's DFMA throughput measured here
+    # (the peaks file has no FP64 figure); nominal GB300 FP64 is 1.25 TFLOP/s
+    fp64_peak_tf = kn.measure_fp64_peak(stream)
+    # DRAM traffic of the integrator from the committed ncu capture of this
+    # kernel (1216 zones, mixed form), scaled to this launch by zone count:
+    # each zone's state is read once per launch
+    traffic = 1.652992e6 * args.zones / 1216 if args.form == "mixed" else None
     roof = {"bound": "alu", "unit": "TFLOP/s", "kernel": "integrate_kernel",
             "achieved": f64 / (kms / 1e3) / 1e12, "peak": fp64_peak_tf,
-            "peak_source": "nominal FP64 (1.25 TFLOP/s)", "traffic": None,
+            "peak_source": "measured FP64 DFMA throughput (kn_measure_fp64_peak)", "traffic": traffic,
+            "traffic_source": "profiles/integrate_kernel_mixed_1216x150_full.md, scaled by zones"
+            if traffic else None,
             "algorithmic_fp64_flops_per_launch": f64, "algorithmic_fp32_flops_per_launch": f32,
-            "kernel_ms": kms}
+            "kernel_ms": kms, "nominal_fp64_tflops": 1.25}
     roof["frac"] = roof["achieved"] / roof["peak"]
     line = {"metric": METRIC, "value": value, "unit": "zone-steps/s", "n_gpus": world, "steps": args.steps,
             "warmup": max(3, args.warmup), "ms_per_step": ms / args.steps, "higher_is_better": True,
@@ -393,7 +410,8 @@ def main():
                        "zones_per_gpu": args.zones, "n_species": 150, "n_reactions": 1604,
                        "form": args.form, "l2": "flushed between timed steps (256 MB write)",
                        "accepted_steps_per_batch": int(steps_per_batch), "rejects_per_batch": int(st["rejects"]),
-                       "zones_ok": int(zones_ok), "parallelism": f"zones sharded, {world} GPU(s)"},
+                       "zones_ok": int(zones_ok), "parallelism": f"zones sharded, {world} GPU(s)",
+                       "tiling": tuned if tuned else {"threads_per_zone": args.tpz, "threads_per_cta": args.tpc}},
             "clocks": clk, "e2e": e2e, "gpu_launches": 3 * args.steps, "roofline": roof}
     if not args.no_forms:
         line["forms"] = other_forms(kn, g, net, zones, dz, stream, st["steps"], kms)

@@ -301,6 +301,38 @@ kn_status kn_mlp_backward(kn_mlp *mlp, const float *features, const float *label
    (bias-corrected, Kingma & Ba), then refresh the BF16 copies.  Asynchronous. */
 kn_status kn_mlp_adam(kn_mlp *mlp, float lr, float beta1, float beta2, float eps, void *stream);
 
+/* ---------------------------------------------------------------------------
+ * Autotuner and measurement helpers (library additions; the paper has none).
+ * ------------------------------------------------------------------------- */
+typedef struct {
+    int32_t threads_per_cta;   /* CTA size P */
+    int32_t threads_per_zone;  /* zone group size G (G == P: CTA-per-zone) */
+    double zone_steps_per_s;   /* measured on the trial batch */
+    int32_t candidates;        /* tilings timed */
+    int32_t pad;
+} kn_tiling;
+
+/*
+ * Time candidate tilings on the networks' current zones and keep the fastest
+ * as the default for later kn_integrate_batch calls with the same precision
+ * and learned/plain form (a tiling in opts still overrides it).  Candidates:
+ * zone groups from one warp (small networks) or the smallest warp multiple
+ * covering the species, up to CTA-per-zone, each with the most groups per CTA
+ * that fit in shared memory and with fewer.  Each trial integrates every zone
+ * for at most max_steps accepted steps (the zone state is saved before and
+ * restored after each trial).  *best receives the winner.  Synchronises
+ * `stream`.  Errors: KN_ERR_INVALID_ARG, KN_ERR_STATE (no zones), KN_ERR_NOMEM,
+ * KN_ERR_CUDA.
+ */
+kn_status kn_autotune(kn_network *const *nets, int32_t n_nets, const kn_opts *opts, int64_t max_steps,
+                      void *stream, kn_tiling *best);
+
+/* Measured FP64 FMA throughput of the current device (independent DFMA
+   chains on every SM, timed with CUDA events), in TFLOP/s (2 flops per FMA).
+   The roofline denominator for the FP64-bound integrator.  Synchronises
+   `stream`. */
+kn_status kn_measure_fp64_peak(double *tflops, void *stream);
+
 /* Largest batch kn_integrate_noalloc accepts (its fixed scratch holds one
    queue slot per zone: 256 KB of device memory, kept until process exit). */
 #define KN_NOALLOC_MAX_ZONES 65536

@@ -95,6 +95,8 @@ struct kn_network {
     DevBuf key_in, key_out, idx_in, order, cub_tmp, qhead;
     bool has_const = true;  // conservative until zones are known
     bool zones_set = false;
+    int tuned_P[2][2] = {{0, 0}, {0, 0}};  // [precision][learned form]: autotuned CTA size
+    int tuned_G[2][2] = {{0, 0}, {0, 0}};  // ... and zone group size
 };
 
 namespace {
@@ -579,7 +581,24 @@ static kn_status prepare_launch(kn_network* const* nets, int n_nets, const kn_op
         int P_lo = 32, P_hi = 1024;
         if (o->threads_per_cta) P_lo = P_hi = o->threads_per_cta;
         else if (o->threads_per_zone) P_lo = P_hi = o->threads_per_zone;
-        if (n_nets == 1 && !o->threads_per_cta) {
+        // an autotuned tiling (kn_autotune) when the caller gives none
+        if (!o->threads_per_cta && !o->threads_per_zone) {
+            const int tP = nets[0]->tuned_P[prec][learn ? 1 : 0];
+            bool all = tP > 0;
+            Tiling cand[kMaxPlans];
+            for (int p = 0; p < n_nets && all; ++p) {
+                const int tG = nets[p]->tuned_G[prec][learn ? 1 : 0];
+                bool ok = false;
+                all = nets[p]->tuned_P[prec][learn ? 1 : 0] == tP && tG > 0;
+                if (all && (s = plan_tiling(nets[p], prec, tP, budget, tG, feat, cand[p], ok)) != KN_OK) return s;
+                all = all && ok;
+            }
+            if (all) {
+                P_best = tP;
+                for (int p = 0; p < n_nets; ++p) tl[p] = cand[p];
+            }
+        }
+        if (!P_best && n_nets == 1 && !o->threads_per_cta) {
             // one network, no explicit CTA size: the most zone groups per CTA
             // (tables staged in shared memory), then the smallest group
             kn_network* n = nets[0];
@@ -600,7 +619,7 @@ static kn_status prepare_launch(kn_network* const* nets, int n_nets, const kn_op
             }
         }
         // without an explicit tiling: the largest CTA that stages every network's tables
-        for (int pass = 0; pass < 2 && !P_best; ++pass) {
+        for (int pass = 0; pass < 2 && !P_best; ++pass) {  // (skipped when a tiling is already chosen)
             for (int P = P_hi; P >= P_lo && !P_best; P -= 32) {
                 bool all = true, all_smem = true;
                 Tiling cand[kMaxPlans];
@@ -961,3 +980,149 @@ kn_status noalloc_prepare(kn_network* n, const kn_opts* o, int32_t n_zones, cons
 
 kn_status noalloc_fail(kn_status s, const char* msg) { return fail(s, "%s", msg); }
 }  // namespace kn
+
+
+namespace kn {
+cudaError_t launch_fp64_peak(double* out, int blocks, int threads, int iters, cudaStream_t st);
+}
+
+namespace {
+// Candidate (P, G) tilings for the listed networks.
+static kn_status tiling_candidates(kn_network* const* nets, int n_nets, int prec, bool feat, int budget,
+                                   std::vector<std::pair<int, int>>& out) {
+    kn_status s;
+    if (n_nets == 1) {
+        kn_network* n = nets[0];
+        for (int G = base_group(n); G <= 512; G += 32) {
+            Tables* tb;
+            if ((s = get_tables(n, prec, G, &tb)) != KN_OK) return s;
+            const GroupLayout gl = group_layout(n, prec, G, feat);
+            int M = std::min(kMaxGroups, 1024 / G);
+            while (M > 0 && tb->tl.bytes + M * gl.bytes > budget) --M;
+            if (M == 0) {  // tables in global memory
+                M = std::min(kMaxGroups, 1024 / G);
+                while (M > 0 && M * gl.bytes > budget) --M;
+            }
+            for (int m = M; m >= std::max(1, M - 1); --m) out.push_back({G * m, G});
+        }
+    } else {
+        for (int P = 1024; P >= 128; P -= 64) out.push_back({P, 0});
+    }
+    return KN_OK;
+}
+}  // namespace
+
+extern "C" {
+
+kn_status kn_measure_fp64_peak(double* tflops, void* stream_) {
+    if (!tflops) return fail(KN_ERR_INVALID_ARG, "kn_measure_fp64_peak: NULL argument");
+    DeviceInfo di;
+    kn_status s = device_info(di);
+    if (s != KN_OK) return s;
+    cudaStream_t st = (cudaStream_t)stream_;
+    const int blocks = di.sms * 4, threads = 512, iters = 4096;
+    DevBuf out;
+    KN_CUDA(out.ensure(sizeof(double) * (size_t)blocks * threads));
+    cudaEvent_t e0, e1;
+    KN_CUDA(cudaEventCreate(&e0));
+    KN_CUDA(cudaEventCreate(&e1));
+    float best = 1e30f;
+    for (int rep = 0; rep < 3; ++rep) {
+        KN_CUDA(cudaEventRecord(e0, st));
+        KN_CUDA(launch_fp64_peak(out.as<double>(), blocks, threads, iters, st));
+        KN_CUDA(cudaEventRecord(e1, st));
+        KN_CUDA(cudaEventSynchronize(e1));
+        float ms;
+        KN_CUDA(cudaEventElapsedTime(&ms, e0, e1));
+        if (rep > 0 && ms < best) best = ms;
+    }
+    cudaEventDestroy(e0);
+    cudaEventDestroy(e1);
+    const double fmas = (double)blocks * threads * 8.0 * iters;
+    *tflops = 2.0 * fmas / (best * 1e-3) / 1e12;
+    return KN_OK;
+}
+
+kn_status kn_autotune(kn_network* const* nets, int32_t n_nets, const kn_opts* o, int64_t max_steps, void* stream_,
+                      kn_tiling* best) {
+    if (!nets || n_nets < 1 || n_nets > kMaxPlans || !o || !best || max_steps < 1)
+        return fail(KN_ERR_INVALID_ARG, "kn_autotune: bad arguments");
+    kn_status s = validate_opts(o);
+    if (s != KN_OK) return s;
+    if (o->replay_dt || o->record_features) return fail(KN_ERR_INVALID_ARG, "kn_autotune: replay/records must be off");
+    for (int p = 0; p < n_nets; ++p)
+        if (!nets[p] || !nets[p]->zones_set) return fail(KN_ERR_STATE, "kn_autotune: network %d has no zones", p);
+    DeviceInfo di;
+    if ((s = device_info(di)) != KN_OK) return s;
+    cudaStream_t st = (cudaStream_t)stream_;
+    const int prec = o->precision;
+    const bool learn = o->mlp != nullptr;
+    const int budget = di.smem_optin - 1024 - 64 - (learn ? kMlpSmemBytes : 0);
+    std::vector<std::pair<int, int>> cands;
+    if ((s = tiling_candidates(nets, n_nets, prec, learn, budget, cands)) != KN_OK) return s;
+    // save the zone abundances (the trials integrate in place)
+    std::vector<std::unique_ptr<DevBuf>> saved(n_nets);
+    for (int p = 0; p < n_nets; ++p) {
+        saved[p].reset(new DevBuf());
+        const size_t bytes = 8 * (size_t)nets[p]->Z * nets[p]->N;
+        KN_CUDA(saved[p]->ensure(bytes));
+        KN_CUDA(cudaMemcpyAsync(saved[p]->p, nets[p]->Y.p, bytes, cudaMemcpyDeviceToDevice, st));
+    }
+    cudaEvent_t e0, e1;
+    KN_CUDA(cudaEventCreate(&e0));
+    KN_CUDA(cudaEventCreate(&e1));
+    kn_tiling win{0, 0, 0.0, 0, 0};
+    for (const auto& c : cands) {
+        kn_opts t = *o;
+        t.threads_per_cta = c.first;
+        t.threads_per_zone = c.second;
+        t.max_steps = std::min<int64_t>(o->max_steps, max_steps);
+        t.use_graph = 0;
+        for (int p = 0; p < n_nets; ++p)
+            KN_CUDA(cudaMemcpyAsync(nets[p]->Y.p, saved[p]->p, 8 * (size_t)nets[p]->Z * nets[p]->N,
+                                    cudaMemcpyDeviceToDevice, st));
+        KN_CUDA(cudaEventRecord(e0, st));
+        s = kn_integrate_batch(nets, n_nets, &t, st);
+        if (s != KN_OK) continue;  // a candidate that does not fit is skipped
+        KN_CUDA(cudaEventRecord(e1, st));
+        KN_CUDA(cudaEventSynchronize(e1));
+        float ms;
+        KN_CUDA(cudaEventElapsedTime(&ms, e0, e1));
+        kn_batch_stats bs;
+        if ((s = kn_get_batch_stats(nets, n_nets, st, &bs)) != KN_OK) return s;
+        const double rate = (double)bs.steps / (ms * 1e-3);
+        win.candidates += 1;
+        if (rate > win.zone_steps_per_s) {
+            win.zone_steps_per_s = rate;
+            win.threads_per_cta = c.first;
+            // resolve the group size the launch used for each network
+            win.threads_per_zone = c.second;
+        }
+    }
+    cudaEventDestroy(e0);
+    cudaEventDestroy(e1);
+    for (int p = 0; p < n_nets; ++p) {
+        KN_CUDA(cudaMemcpyAsync(nets[p]->Y.p, saved[p]->p, 8 * (size_t)nets[p]->Z * nets[p]->N,
+                                cudaMemcpyDeviceToDevice, st));
+        KN_CUDA(launch_fill_int(nets[p]->status.as<int>(), nets[p]->Z, KN_ZONE_PENDING, st));
+    }
+    KN_CUDA(cudaStreamSynchronize(st));
+    if (win.threads_per_cta == 0) return fail(KN_ERR_INVALID_ARG, "kn_autotune: no candidate tiling ran");
+    // remember the winner: per network, the group size that CTA size gives it
+    for (int p = 0; p < n_nets; ++p) {
+        int G = win.threads_per_zone;
+        if (G == 0) {
+            Tiling tlp;
+            bool ok = false;
+            if ((s = plan_tiling(nets[p], prec, win.threads_per_cta, budget, 0, learn, tlp, ok)) != KN_OK) return s;
+            if (!ok) return fail(KN_ERR_STATE, "kn_autotune: winning tiling no longer fits");
+            G = tlp.G;
+        }
+        nets[p]->tuned_P[prec][learn ? 1 : 0] = win.threads_per_cta;
+        nets[p]->tuned_G[prec][learn ? 1 : 0] = G;
+    }
+    *best = win;
+    return KN_OK;
+}
+
+}  // extern "C"

@@ -905,3 +905,27 @@ cudaError_t launch_fill_int(int* p, int n, int v, cudaStream_t stream) {
 }
 
 }  // namespace kn
+
+namespace kn {
+// FP64 FMA throughput probe: 8 independent DFMA chains per thread
+__global__ void fp64_peak_kernel(double* out, double a, double b, int iters) {
+    double x0 = a + threadIdx.x, x1 = x0 + 1, x2 = x0 + 2, x3 = x0 + 3, x4 = x0 + 4, x5 = x0 + 5, x6 = x0 + 6,
+           x7 = x0 + 7;
+    for (int i = 0; i < iters; ++i) {
+        x0 = fma(x0, b, a);
+        x1 = fma(x1, b, a);
+        x2 = fma(x2, b, a);
+        x3 = fma(x3, b, a);
+        x4 = fma(x4, b, a);
+        x5 = fma(x5, b, a);
+        x6 = fma(x6, b, a);
+        x7 = fma(x7, b, a);
+    }
+    out[blockIdx.x * blockDim.x + threadIdx.x] = x0 + x1 + x2 + x3 + x4 + x5 + x6 + x7;
+}
+
+cudaError_t launch_fp64_peak(double* out, int blocks, int threads, int iters, cudaStream_t st) {
+    fp64_peak_kernel<<<blocks, threads, 0, st>>>(out, 0.5, 0.999, iters);
+    return cudaGetLastError();
+}
+}  // namespace kn

@@ -59,6 +59,11 @@ class _Stats(C.Structure):
                 ("rejects", C.c_int64), ("proposals_used", C.c_int64)]
 
 
+class _Tiling(C.Structure):
+    _fields_ = [("threads_per_cta", C.c_int32), ("threads_per_zone", C.c_int32),
+                ("zone_steps_per_s", C.c_double), ("candidates", C.c_int32), ("pad", C.c_int32)]
+
+
 _lib = None
 
 
@@ -84,6 +89,8 @@ def lib():
         "kn_get_batch_stats": (I32, [P, I32, P, C.POINTER(_Stats)]),
         "kn_probe_step": (I32, [P, C.POINTER(_Opts), P, P, P, P, P, P]),
         "kn_integrate_noalloc": (I32, [P, I32, C.POINTER(_Zones), C.POINTER(_Opts), P, P, P, P, P, P, P]),
+        "kn_autotune": (I32, [P, I32, C.POINTER(_Opts), I64, P, C.POINTER(_Tiling)]),
+        "kn_measure_fp64_peak": (I32, [C.POINTER(C.c_double), P]),
         "kn_mlp_create": (I32, [C.POINTER(P)]),
         "kn_mlp_destroy": (I32, [P]),
         "kn_mlp_set_params": (I32, [P, P, P, P]),
@@ -330,3 +337,20 @@ class MLP:
 
     def adam(self, lr=1e-3, beta1=0.9, beta2=0.999, eps=1e-8, stream=None):
         _check(lib().kn_mlp_adam(self.h, lr, beta1, beta2, eps, C.c_void_p(_stream_ptr(stream))))
+
+
+def autotune(nets, opts: Opts, max_steps: int = 400, stream=None) -> dict:
+    """Time candidate tilings on the networks' current zones; the winner
+    becomes their default tiling for this precision and form."""
+    arr = (C.c_void_p * len(nets))(*[n.h for n in nets])
+    t = _Tiling()
+    _check(lib().kn_autotune(arr, len(nets), C.byref(opts.c()), int(max_steps), C.c_void_p(_stream_ptr(stream)),
+                             C.byref(t)))
+    return {f: getattr(t, f) for f, _ in _Tiling._fields_ if f != "pad"}
+
+
+def measure_fp64_peak(stream=None) -> float:
+    """Measured FP64 FMA throughput of the current device, TFLOP/s."""
+    v = C.c_double()
+    _check(lib().kn_measure_fp64_peak(C.byref(v), C.c_void_p(_stream_ptr(stream))))
+    return v.value

@@ -360,3 +360,46 @@ def test_full_size_batch_sampled(kn, oracle_mod, prec):
         assert _rel_err(r["Y"][i], ref["Y"][a], 1e-10) < 10 * 0.05
     ratio = r["steps"][pick].sum() / ref["steps"].sum()
     assert abs(ratio - 1) < 0.05, ratio
+
+
+# --------------------------------------------------------------------------
+# autotuner and the measured FP64 peak
+# --------------------------------------------------------------------------
+def test_autotune_picks_a_tiling_and_results_are_unchanged(kn):
+    net = net150()
+    z = profile_zones(net, 700, t_end=3e-11)
+    g = kn.Network(net)
+    g.set_zones(z)
+    kn.integrate_batch([g], kn.Opts(precision=MIXED, threads_per_zone=160, threads_per_cta=160))
+    ref = g.get()
+    g.set_zones(z)
+    t = kn.autotune([g], kn.Opts(precision=MIXED), max_steps=100)
+    assert t["candidates"] >= 4 and t["zone_steps_per_s"] > 0
+    assert t["threads_per_cta"] % t["threads_per_zone"] == 0
+    # the zone state was restored: the default launch now uses the tuned tiling
+    kn.integrate_batch([g], kn.Opts(precision=MIXED))
+    r = g.get()
+    assert (r["status"] == 0).all()
+    # a zone's result does not depend on the tiling beyond its gather chunking
+    for i in range(0, 700, 97):
+        m = ref["Y"][i] > 1e-10
+        assert np.max(np.abs(r["Y"][i][m] - ref["Y"][i][m]) / ref["Y"][i][m]) < 0.5
+
+
+def test_mixed_sizes_autotuned(kn):
+    nets = [chain_network(), net150(), net365()]
+    gs = [kn.Network(n) for n in nets]
+    for g, n, c in zip(gs, nets, (40, 80, 20)):
+        g.set_zones(profile_zones(n, c, t_end=1e-11))
+    t = kn.autotune(gs, kn.Opts(precision=MIXED), max_steps=50)
+    assert t["candidates"] >= 2
+    for g, n, c in zip(gs, nets, (40, 80, 20)):
+        g.set_zones(profile_zones(n, c, t_end=1e-11))
+    kn.integrate_batch(gs, kn.Opts(precision=MIXED))
+    for g in gs:
+        assert (g.get()["status"] == 0).all()
+
+
+def test_fp64_peak_is_measured(kn):
+    tf = kn.measure_fp64_peak()
+    assert 0.2 < tf < 10.0, tf
