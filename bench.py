@@ -297,8 +297,10 @@ def main():
         dist.barrier()
     build.build()
     net = net150()
-    # weak scaling: each rank integrates its own batch of zones (seeds differ by rank)
-    zones = profile_zones(net, args.zones, base_seed=1000 + rank * args.zones, t_end=args.t_end)
+    # weak scaling: each rank integrates its own slice of the global batch
+    from paper_1409_5826_gb300 import shard
+    zones = profile_zones(net, args.zones, base_seed=shard.zone_seed_base(rank, world, args.zones),
+                          t_end=args.t_end)
     dev = torch.device("cuda", local)
     names = ("Y0", "T0", "rho0", "tau", "t_start", "t_end", "dt_trial")
     dz = {k: torch.from_numpy(np.ascontiguousarray(getattr(zones, k))).to(dev) for k in names}
@@ -345,15 +347,7 @@ def main():
     st = kn.batch_stats([g], stream)
     steps_per_batch = st["steps"]
     zones_ok = st["zones_ok"]
-    if world > 1:
-        t = torch.tensor([ms], device=dev)
-        dist.all_reduce(t, op=dist.ReduceOp.MAX)
-        ms = float(t.item())
-        c = torch.tensor([steps_per_batch, zones_ok], device=dev, dtype=torch.float64)
-        dist.all_reduce(c)
-        steps_all, zones_all = c.tolist()
-    else:
-        steps_all, zones_all = steps_per_batch, zones_ok
+    ms, steps_all, zones_all = shard.aggregate(ms, steps_per_batch, zones_ok, device=dev)
     value = steps_all * args.steps / (ms / 1e3)
 
     # end to end through the public API with pinned host buffers

@@ -370,6 +370,32 @@ kn_status kn_integrate_noalloc(kn_network *net, int32_t n_zones, const kn_zone_c
                                const kn_opts *opts, double *Y, double *t, double *dt_next,
                                int64_t *steps, int64_t *rejects, int32_t *status, void *stream);
 
+/*
+ * Operator splitting (Sec. 4, Sec. 6): continue every zone of `net` into the
+ * next hydro interval.  The abundances stay where the last integration left
+ * them; each zone starts at its last time t, runs to t_end[z] at constant
+ * T9[z], rho[z] (the hydro values held fixed over the interval), and takes
+ * the last dt_next as its trial step.  Arrays [n_zones] host or device (mem),
+ * n_zones must equal the zones set.  Asynchronous on `stream`.
+ * Errors: KN_ERR_INVALID_ARG, KN_ERR_STATE (no zones), KN_ERR_CUDA.
+ */
+kn_status kn_advance_zones(kn_network *net, int32_t n_zones, const double *T9, const double *rho,
+                           const double *t_end, int32_t mem, void *stream);
+
+/*
+ * Integrated energy release (Sec. 6 item 3).  With per-species binding
+ * energies B_i (any unit per nucleus; host array [n_species]) set, every
+ * integration also records per zone E = sum_i B_i (Y_i(t) - Y_i(t_start)),
+ * which for an A-conserving network equals the time integral of
+ * sum_j Q_j f_j with Q_j the reaction's binding-energy gain.  Synchronous.
+ */
+kn_status kn_set_binding_energies(kn_network *net, const double *B);
+
+/* Copy the per-zone energy release of the last integration (see above) to
+   E [n_zones] (host or device per mem); synchronises `stream`.  Zones without
+   binding energies set report 0. */
+kn_status kn_get_energy(const kn_network *net, double *E, int32_t mem, void *stream);
+
 /* Human-readable description of the most recent failure on this host thread
    (empty string if none).  The pointer stays valid until the next call on
    the same thread. */

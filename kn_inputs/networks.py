@@ -286,3 +286,14 @@ def random_tiny_network(n_species: int, n_reactions: int, seed: int,
     ln_k0 = [lnk_lo + rng.uniform() * (lnk_hi - lnk_lo) for _ in reactions]
     return custom_network(A, reactions, ln_k0, [0.0] * len(reactions),
                           init_X={1: 1.0}, name=f"tiny{n_species}_{len(reactions)}_{seed}")
+
+
+def binding_energies(net: Network, seed: int = 17) -> np.ndarray:
+    """Synthetic per-species binding energies (MeV): A times a binding-per-nucleon
+    curve peaking at A = 56 (8.8 MeV), with a seeded 1 % scatter.  Input data
+    only (the rate library carries no energies)."""
+    rng = SplitMix64(seed)
+    A = net.A
+    b = 8.8 - 2.0 * ((A - 56.0) / 56.0) ** 2 - 6.0 / np.sqrt(A)
+    scatter = np.array([1.0 + 0.01 * (2.0 * rng.uniform() - 1.0) for _ in range(len(A))])
+    return A * np.maximum(b, 0.5) * scatter

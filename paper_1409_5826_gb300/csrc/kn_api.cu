@@ -91,7 +91,9 @@ struct kn_network {
     std::map<std::pair<int, int>, Tables> tables;  // (precision, Q) -> device blob
     // zone state
     int Z = 0, capZ = 0;
-    DevBuf Y, T0, rho0, tau, ts, te, dtt, tout, dtn, steps, rej, props, status;
+    DevBuf Y, T0, rho0, tau, ts, te, dtt, tout, dtn, steps, rej, props, status, energy;
+    DevBuf bind;            // [N] binding energies, when set
+    bool has_bind = false;
     DevBuf key_in, key_out, idx_in, order, cub_tmp, qhead;
     bool has_const = true;  // conservative until zones are known
     bool zones_set = false;
@@ -497,6 +499,7 @@ kn_status kn_set_zone_conditions(kn_network* n, int32_t Z, const kn_zone_conditi
         KN_CUDA(n->steps.ensure(zd));
         KN_CUDA(n->rej.ensure(zd));
         KN_CUDA(n->props.ensure(zd));
+        KN_CUDA(n->energy.ensure(zd));
         KN_CUDA(n->status.ensure(4 * (size_t)Z));
         KN_CUDA(n->key_in.ensure(4 * (size_t)Z));
         KN_CUDA(n->key_out.ensure(4 * (size_t)Z));
@@ -518,6 +521,7 @@ kn_status kn_set_zone_conditions(kn_network* n, int32_t Z, const kn_zone_conditi
     KN_CUDA(cudaMemcpyAsync(n->te.p, zc->t_end, zd, kind, st));
     KN_CUDA(cudaMemcpyAsync(n->dtt.p, zc->dt_trial, zd, kind, st));
     KN_CUDA(launch_fill_int(n->status.as<int>(), Z, KN_ZONE_PENDING, st));
+    KN_CUDA(cudaMemsetAsync(n->energy.p, 0, 8 * (size_t)Z, st));
     // work-queue order: predicted longest zones first
     KN_CUDA(launch_zone_cost_simple(n->T0.as<double>(), n->rho0.as<double>(), Z, n->nbar, n->rbar,
                                     n->key_in.as<float>(), n->idx_in.as<int>(), st));
@@ -678,6 +682,8 @@ static kn_status prepare_launch(kn_network* const* nets, int n_nets, const kn_op
         P.steps = n->steps.as<long long>();
         P.rejects = n->rej.as<long long>();
         P.props = n->props.as<long long>();
+        P.bind = n->has_bind ? n->bind.as<const double>() : nullptr;
+        P.energy = n->energy.as<double>();
         P.status = n->status.as<int>();
         P.n_zones = n->Z;
         P.zone_base = zone_base;
@@ -1122,6 +1128,68 @@ kn_status kn_autotune(kn_network* const* nets, int32_t n_nets, const kn_opts* o,
         nets[p]->tuned_G[prec][learn ? 1 : 0] = G;
     }
     *best = win;
+    return KN_OK;
+}
+
+}  // extern "C"
+
+
+namespace kn {
+cudaError_t launch_advance(int n, const double* T9, const double* rho, const double* te, const double* t_out,
+                           const double* dt_next, double* T0, double* rho0, double* tau, double* ts, double* tend,
+                           double* dtt, int* status, cudaStream_t st);
+}
+
+extern "C" {
+
+kn_status kn_advance_zones(kn_network* n, int32_t Z, const double* T9, const double* rho, const double* t_end,
+                           int32_t mem, void* stream_) {
+    if (!n || !T9 || !rho || !t_end) return fail(KN_ERR_INVALID_ARG, "kn_advance_zones: NULL argument");
+    if (!n->zones_set) return fail(KN_ERR_STATE, "kn_advance_zones: no zones set");
+    if (Z != n->Z) return fail(KN_ERR_INVALID_ARG, "kn_advance_zones: n_zones %d != zones set %d", Z, n->Z);
+    if (mem != KN_MEM_HOST && mem != KN_MEM_DEVICE) return fail(KN_ERR_INVALID_ARG, "bad kn_mem");
+    cudaStream_t st = (cudaStream_t)stream_;
+    const double *dT = T9, *dR = rho, *dE = t_end;
+    DevBuf tmp;
+    if (mem == KN_MEM_HOST) {
+        for (int z = 0; z < Z; ++z)
+            if (!(std::isfinite(T9[z]) && T9[z] > 0 && std::isfinite(rho[z]) && rho[z] > 0 && std::isfinite(t_end[z])))
+                return fail(KN_ERR_INVALID_ARG, "kn_advance_zones: zone %d needs finite T9, rho > 0 and t_end", z);
+        KN_CUDA(tmp.ensure(3 * 8 * (size_t)Z));
+        double* p = tmp.as<double>();
+        KN_CUDA(cudaMemcpyAsync(p, T9, 8 * (size_t)Z, cudaMemcpyHostToDevice, st));
+        KN_CUDA(cudaMemcpyAsync(p + Z, rho, 8 * (size_t)Z, cudaMemcpyHostToDevice, st));
+        KN_CUDA(cudaMemcpyAsync(p + 2 * Z, t_end, 8 * (size_t)Z, cudaMemcpyHostToDevice, st));
+        dT = p;
+        dR = p + Z;
+        dE = p + 2 * Z;
+    }
+    KN_CUDA(launch_advance(Z, dT, dR, dE, n->tout.as<double>(), n->dtn.as<double>(), n->T0.as<double>(),
+                           n->rho0.as<double>(), n->tau.as<double>(), n->ts.as<double>(), n->te.as<double>(),
+                           n->dtt.as<double>(), n->status.as<int>(), st));
+    KN_CUDA(cudaMemsetAsync(n->energy.p, 0, 8 * (size_t)Z, st));
+    n->has_const = true;
+    if (mem == KN_MEM_HOST) KN_CUDA(cudaStreamSynchronize(st));  // tmp is freed on return
+    return KN_OK;
+}
+
+kn_status kn_set_binding_energies(kn_network* n, const double* B) {
+    if (!n || !B) return fail(KN_ERR_INVALID_ARG, "kn_set_binding_energies: NULL argument");
+    for (int i = 0; i < n->N; ++i)
+        if (!std::isfinite(B[i])) return fail(KN_ERR_INVALID_ARG, "kn_set_binding_energies: B[%d] not finite", i);
+    KN_CUDA(n->bind.ensure(8 * (size_t)n->N));
+    KN_CUDA(cudaMemcpy(n->bind.p, B, 8 * (size_t)n->N, cudaMemcpyHostToDevice));
+    n->has_bind = true;
+    return KN_OK;
+}
+
+kn_status kn_get_energy(const kn_network* n, double* E, int32_t mem, void* stream_) {
+    if (!n || !E) return fail(KN_ERR_INVALID_ARG, "kn_get_energy: NULL argument");
+    if (!n->zones_set) return fail(KN_ERR_STATE, "kn_get_energy: no zones set");
+    cudaStream_t st = (cudaStream_t)stream_;
+    KN_CUDA(cudaMemcpyAsync(E, n->energy.p, 8 * (size_t)n->Z,
+                            mem == KN_MEM_HOST ? cudaMemcpyDeviceToHost : cudaMemcpyDeviceToDevice, st));
+    KN_CUDA(cudaStreamSynchronize(st));
     return KN_OK;
 }
 

@@ -753,12 +753,28 @@ __device__ void run_group(const PlanDev& P, const OptsDev& O, const unsigned cha
             gs.sync();
         }
 
-        // ---- write back (Sec. 6 step 3 outputs) ----
+        // ---- write back (Sec. 6 step 3 outputs: abundances, energy, final dt) ----
         if (!O.probe) {
             const double* Yc = Y64 + S.cur * NP1;
             double* Yg = P.Y + (size_t)z * N;
-            if (S.status != 5)
-                for (int i = lane; i < N; i += G) Yg[i] = Yc[i];
+            double e = 0.0;
+            if (S.status != 5) {
+                for (int i = lane; i < N; i += G) {
+                    if (P.bind) e = fma(P.bind[i], Yc[i] - Yg[i], e);  // Yg still holds Y(t_start)
+                    Yg[i] = Yc[i];
+                }
+            }
+            if (P.bind) {
+#pragma unroll
+                for (int off = 16; off > 0; off >>= 1) e += __shfl_xor_sync(0xffffffffu, e, off);
+                if ((lane & 31) == 0) g.red_c[lane >> 5] = e;
+                gs.sync();
+                if (lane == 0) {
+                    double es = 0.0;
+                    for (int w = 0; w < (G >> 5); ++w) es += g.red_c[w];
+                    P.energy[z] = es;
+                }
+            }
             if (lane == 0) {
                 P.t_out[z] = S.t;
                 P.dt_next[z] = S.dt;
@@ -926,6 +942,32 @@ __global__ void fp64_peak_kernel(double* out, double a, double b, int iters) {
 
 cudaError_t launch_fp64_peak(double* out, int blocks, int threads, int iters, cudaStream_t st) {
     fp64_peak_kernel<<<blocks, threads, 0, st>>>(out, 0.5, 0.999, iters);
+    return cudaGetLastError();
+}
+}  // namespace kn
+
+namespace kn {
+// operator-split continuation: the next hydro interval starts where the last ended
+__global__ void advance_kernel(int n, const double* T9, const double* rho, const double* te, const double* t_out,
+                               const double* dt_next, double* T0, double* rho0, double* tau, double* ts, double* tend,
+                               double* dtt, int* status) {
+    const int z = blockIdx.x * blockDim.x + threadIdx.x;
+    if (z < n) {
+        T0[z] = T9[z];
+        rho0[z] = rho[z];
+        tau[z] = 0.0;
+        ts[z] = t_out[z];
+        tend[z] = te[z];
+        dtt[z] = dt_next[z];
+        status[z] = 6;  // PENDING
+    }
+}
+
+cudaError_t launch_advance(int n, const double* T9, const double* rho, const double* te, const double* t_out,
+                           const double* dt_next, double* T0, double* rho0, double* tau, double* ts, double* tend,
+                           double* dtt, int* status, cudaStream_t st) {
+    advance_kernel<<<(n + 255) / 256, 256, 0, st>>>(n, T9, rho, te, t_out, dt_next, T0, rho0, tau, ts, tend, dtt,
+                                                    status);
     return cudaGetLastError();
 }
 }  // namespace kn

@@ -106,6 +106,8 @@ struct PlanDev {
     long long* steps;
     long long* rejects;
     long long* props;            // [Z] accepted steps proposed by the network
+    const double* bind;          // [N] binding energies (NULL: no energy output)
+    double* energy;              // [Z] sum_i B_i (Y_end - Y_start)
     int* status;
     int32_t n_zones;
     int32_t zone_base;           // first global zone index of this plan (replay arrays)

@@ -90,6 +90,9 @@ def lib():
         "kn_probe_step": (I32, [P, C.POINTER(_Opts), P, P, P, P, P, P]),
         "kn_integrate_noalloc": (I32, [P, I32, C.POINTER(_Zones), C.POINTER(_Opts), P, P, P, P, P, P, P]),
         "kn_autotune": (I32, [P, I32, C.POINTER(_Opts), I64, P, C.POINTER(_Tiling)]),
+        "kn_advance_zones": (I32, [P, I32, P, P, P, I32, P]),
+        "kn_set_binding_energies": (I32, [P, P]),
+        "kn_get_energy": (I32, [P, P, I32, P]),
         "kn_measure_fp64_peak": (I32, [C.POINTER(C.c_double), P]),
         "kn_mlp_create": (I32, [C.POINTER(P)]),
         "kn_mlp_destroy": (I32, [P]),
@@ -246,6 +249,23 @@ class Network:
         ptrs = [out[k].data_ptr() if k in out else None for k in keys]
         _check(lib().kn_get_abundances(self.h, *ptrs, MEM_DEVICE, C.c_void_p(_stream_ptr(stream))))
         return out
+
+    def advance(self, T9, rho, t_end, stream=None):
+        """Operator splitting: continue every zone into the next hydro interval at
+        constant T9, rho (host arrays [Z]), carrying its last dt_next."""
+        a = [_host(x, np.float64) for x in (T9, rho, t_end)]
+        _check(lib().kn_advance_zones(self.h, self.Z, *[x.ctypes.data for x in a], MEM_HOST,
+                                      C.c_void_p(_stream_ptr(stream))))
+
+    def set_binding_energies(self, B):
+        B = _host(B, np.float64)
+        assert B.shape == (self.N,)
+        _check(lib().kn_set_binding_energies(self.h, B.ctypes.data))
+
+    def energy(self, stream=None) -> np.ndarray:
+        E = np.empty(self.Z)
+        _check(lib().kn_get_energy(self.h, E.ctypes.data, MEM_HOST, C.c_void_p(_stream_ptr(stream))))
+        return E
 
     def probe(self, opts: Opts, stream=None):
         """One step from each zone's initial state (no accept test): F+, k, Y1, cons, rel."""

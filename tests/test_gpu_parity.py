@@ -403,3 +403,45 @@ def test_mixed_sizes_autotuned(kn):
 def test_fp64_peak_is_measured(kn):
     tf = kn.measure_fp64_peak()
     assert 0.2 < tf < 10.0, tf
+
+
+# --------------------------------------------------------------------------
+# operator splitting and energy release (Sec. 4, Sec. 6)
+# --------------------------------------------------------------------------
+@pytest.mark.parametrize("prec", [FP64, MIXED])
+def test_operator_split_chain_and_energy(kn, oracle_mod, prec):
+    from kn_inputs import Zones, binding_energies
+    from paper_1409_5826_gb300 import opsplit
+    net = net150()
+    B = binding_energies(net)
+    Z = 12
+    z = profile_zones(net, Z, t_end=1e-11)
+    edges = [1e-12, 4e-12, 1e-11, 2e-11, 4e-11]
+    schedule = []
+    for k in range(len(edges) - 1):
+        schedule.append((z.T0 * (1 - 0.04 * k), z.rho0 * (1 - 0.08 * k), np.full(Z, edges[k + 1])))
+    g = kn.Network(net)
+    g.set_binding_energies(B)
+    host_calls = []
+    res = opsplit.run(g, z, schedule, kn.Opts(precision=prec), host_step=host_calls.append)
+    assert host_calls == list(range(len(schedule)))
+    orc = oracle_mod.Oracle(net)
+    for i in range(Z):
+        Y = z.Y0[i].copy()
+        dt = z.dt_trial[i]
+        for k, (T9, rho, te) in enumerate(schedule):
+            zk = Zones(Y0=Y[None, :], T0=np.array([T9[i]]), rho0=np.array([rho[i]]), tau=np.zeros(1),
+                       t_start=np.array([edges[k]]), t_end=np.array([te[i]]), dt_trial=np.array([dt]))
+            r = orc.integrate(zk, 0)
+            assert r["status"] == 0
+            Ynew, dt = r["Y"], r["dt_next"]
+            got = res[k]
+            assert got["status"][i] == 0 and got["t"][i] == te[i]
+            m = Ynew > 1e-10
+            assert np.max(np.abs(got["Y"][i][m] - Ynew[m]) / Ynew[m]) < 10 * 0.05
+            # energy of this interval: the GPU's own identity, then against the oracle's
+            y_before = z.Y0[i] if k == 0 else res[k - 1]["Y"][i]
+            assert got["energy"][i] == pytest.approx(float(B @ (got["Y"][i] - y_before)), rel=1e-9, abs=1e-12)
+            e_ref = float(B @ (Ynew - Y))
+            assert got["energy"][i] == pytest.approx(e_ref, rel=0.05, abs=1e-3 * abs(e_ref) + 1e-6)
+            Y = Ynew

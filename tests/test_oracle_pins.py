@@ -414,3 +414,27 @@ def test_status_codes(oracle_mod):
     zz.Y0[0, 5] = np.nan
     r = orc.integrate(zz, 0, oracle_mod.OracleOpts(max_reject=3))
     assert r["status"] == 3
+
+
+def test_energy_release_telescopes(oracle_mod):
+    """sum_i B_i (Y_end - Y_start) equals sum over steps of dt sum_j Q_j f_j,
+    Q_j = sum_products B - sum_reactants B, exactly under forward Euler (every
+    species on that branch), since dY_i = dt sum_j nu_ij f_j."""
+    from kn_inputs import binding_energies
+    net = net150()
+    orc = oracle_mod.Oracle(net)
+    B = binding_energies(net)
+    Q = np.array([B[p[p >= 0]].sum() - B[r[r >= 0]].sum() for r, p in zip(net.reac, net.prod)])
+    z = constant_zones(net)
+    k = orc.rates(3.0, 1e8)
+    _, kk, _ = orc.rhs(k, z.Y0[0])
+    h = 0.2 / kk.max()
+    Y = z.Y0[0].copy()
+    flux_sum = 0.0
+    for _ in range(50):
+        _, _, f = orc.rhs(k, Y)
+        flux_sum += h * float(np.dot(Q, f))
+        Y, _ = orc.replay(type(z)(Y0=Y[None, :], T0=z.T0, rho0=z.rho0, tau=z.tau, t_start=z.t_start,
+                                   t_end=np.array([1.0]), dt_trial=z.dt_trial), 0, [h],
+                          opts=oracle_mod.OracleOpts(kappa=1e300))
+    assert float(np.dot(B, Y - z.Y0[0])) == pytest.approx(flux_sum, rel=1e-9)
