@@ -562,6 +562,22 @@ static kn_status validate_opts(const kn_opts* o) {
     return KN_OK;
 }
 
+// FP32 guard band of the mixed form's accept test.  y, y', their max m and the
+// difference d of the FP32 copies carry relative errors of at most 2^-24 each,
+// so |d32 - d| <= 2^-23 m + 2^-24 |d|; near the threshold |d| ~ eps_r m this is
+// a relative error of 2^-23 / eps_r + 2^-24, plus the roundings of eps_r and
+// eps_r m.  Outside 8x that band the FP32 compare decides as the FP64 one does.
+static void set_guard_band(OptsDev& D, const kn_opts* o) {
+    const double u = 5.9604644775390625e-08;  // 2^-24
+    const double band = 8.0 * (2.0 * u / o->eps_r + 4.0 * u);
+    D.eps_r32 = (float)o->eps_r;
+    D.kappa32 = (float)o->kappa;
+    D.band_lo32 = (float)(1.0 - band);
+    D.band_hi32 = (float)(1.0 + band);
+    D.ymin_lo32 = (float)(o->y_min * (1.0 - 8.0 * u));
+    D.ymin_hi32 = (float)(o->y_min * (1.0 + 8.0 * u));
+}
+
 // Fill lp for the listed networks; returns grid/block.
 static kn_status prepare_launch(kn_network* const* nets, int n_nets, const kn_opts* o, LaunchParams& lp,
                                 int& grid, int& block, bool probe) {
@@ -734,6 +750,7 @@ static kn_status prepare_launch(kn_network* const* nets, int n_nets, const kn_op
     D.max_steps = o->max_steps;
     D.max_reject = o->max_reject;
     D.lockstep = o->lockstep;
+    set_guard_band(D, o);
     D.replay_dt = o->replay_dt;
     D.replay_off = (const long long*)o->replay_off;
     D.replay_len = (const long long*)o->replay_len;
@@ -979,6 +996,7 @@ kn_status noalloc_prepare(kn_network* n, const kn_opts* o, int32_t n_zones, cons
     D.dt_min_frac = o->dt_min_frac;
     D.max_steps = o->max_steps;
     D.max_reject = o->max_reject;
+    set_guard_band(D, o);
     nbar = n->nbar;
     rbar = n->rbar;
     return KN_OK;

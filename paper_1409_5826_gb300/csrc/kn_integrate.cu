@@ -165,26 +165,59 @@ __device__ __forceinline__ void update_reduce(const PlanDev& P, const OptsDev& O
     float* Yn32 = g.Y32 + (cur ^ 1) * NP1;
     const float* Yc32 = g.Y32 + cur * NP1;
     const double kappa = O.kappa, ymin = O.y_min, eps_r = O.eps_r;
+    [[maybe_unused]] const float h32 = PREC == kPrecMixed ? (float)h : 0.f;
     double csum = 0.0, bn = 0.0, bd = 1.0;
     float rmax = 0.f;
     int ok = 1;
     for (int i = lane; i < N; i += G) {
-        const double y = Yc[i], fp = (double)Fk[i], kk = (double)Fk[N + i];
-        const double kdt = kk * h;
-        const double yn = (kdt >= kappa) ? (y + h * fp) / (1.0 + kdt) : y + h * (fp - kk * y);
+        const double y = Yc[i];
+        double yn;
+        float yn32 = 0.f, y32 = 0.f;
+        if (PREC == kPrecMixed) {
+            // Eq. 3 in FP32, the precision F+ and k arrive in: on the
+            // asymptotic branch y' itself (relative accuracy, positivity), on
+            // the explicit branch the change dt (F+ - k y), added to the FP64
+            // abundance so that small changes accumulate without loss.
+            const float fp32 = Fk[i], kk32 = Fk[N + i];
+            y32 = Yc32[i];
+            const float kdt32 = kk32 * h32;
+            const bool asym = kdt32 >= O.kappa32;
+            const float v = asym ? __fdiv_rn(fmaf(h32, fp32, y32), 1.f + kdt32) : h32 * fmaf(-kk32, y32, fp32);
+            const double v64 = (double)v;
+            yn = asym ? v64 : y + v64;
+            yn32 = asym ? v : (float)yn;
+            Yn32[i] = yn32;
+        } else {
+            const double fp = (double)Fk[i], kk = (double)Fk[N + i];
+            const double kdt = kk * h;
+            yn = (kdt >= kappa) ? (y + h * fp) / (1.0 + kdt) : y + h * (fp - kk * y);
+        }
         Yn64[i] = yn;
         const double d = yn - y;
         csum = fma(g.A[i], d, csum);
-        const double m = y > yn ? y : yn;
         if (PREC == kPrecMixed) {
-            const float yn32 = (float)yn;
-            Yn32[i] = yn32;
-            if (m > ymin) {
-                ok &= fabs(d) <= eps_r * m ? 1 : 0;  // the accept test, FP64
-                const float y32 = Yc32[i];           // the dt proposal, FP32
-                rmax = fmaxf(rmax, __fdividef(fabsf(yn32 - y32), fmaxf(y32, yn32)));
+            // The accept test's decisions are those of the FP64 compares
+            // m > y_min and |d| <= eps_r m; they are taken on the FP32 copies
+            // when the FP32 values lie clearly on one side (outside a guard
+            // band that bounds the FP32 rounding of y, y', d and m), and in
+            // FP64 inside the band.
+            const float m32 = fmaxf(y32, yn32);
+            int tested;
+            if (m32 > O.ymin_hi32) tested = 1;
+            else if (m32 < O.ymin_lo32) tested = 0;
+            else tested = (y > yn ? y : yn) > ymin;
+            if (tested) {
+                const float d32 = fabsf(yn32 - y32);
+                const float lim = O.eps_r32 * m32;
+                int pass_i;
+                if (d32 < __fmul_rn(lim, O.band_lo32)) pass_i = 1;
+                else if (d32 > __fmul_rn(lim, O.band_hi32)) pass_i = 0;
+                else pass_i = fabs(d) <= eps_r * (y > yn ? y : yn);
+                ok &= pass_i;
+                rmax = fmaxf(rmax, __fdividef(d32, m32));  // the dt proposal, FP32
             }
-        } else if (m > ymin) {
+        } else if ((y > yn ? y : yn) > ymin) {
+            const double m = y > yn ? y : yn;
             const double ad = fabs(d);
             if (ad * bd > bn * m) {
                 bn = ad;
@@ -192,8 +225,8 @@ __device__ __forceinline__ void update_reduce(const PlanDev& P, const OptsDev& O
             }
         }
         if (O.probe) {
-            O.probe_Fp[(size_t)z * N + i] = fp;
-            O.probe_k[(size_t)z * N + i] = kk;
+            O.probe_Fp[(size_t)z * N + i] = (double)Fk[i];
+            O.probe_k[(size_t)z * N + i] = (double)Fk[N + i];
             O.probe_Y1[(size_t)z * N + i] = yn;
         }
     }
@@ -367,6 +400,76 @@ __device__ float mlp_forward_group(const OptsDev& O, const GroupPtrs& g, const u
     return s + Pb[384];
 }
 
+// (a) rates k_j(t), fluxes f_j and reactant-slot partials (Eq. 1) of the state
+// in buffer `buf`, over reactions j0, j0 + stride, ...; reactions are sorted
+// 1-, 2-, 3-body, so no multiply by an absent reactant.  s = t / tau (FP64
+// form: poly selects the series for exp(-c_j s)); u = s / ln 2 (mixed form).
+template <int PREC>
+__device__ __forceinline__ void flux_pass(const PlanDev& P, const GroupPtrs& g, int j0, int stride, int buf,
+                                          int constant, double s, float u, int poly) {
+    using real = typename PrecTraits<PREC>::real;
+    const int N = P.N, R = P.R, R1 = P.R1, R12 = P.R12, NP1 = N + 1;
+    const ushort4* __restrict__ rspec = g.rspec;
+    const real* __restrict__ cexp = (const real*)g.cexp;
+    const real* __restrict__ Kz = (const real*)g.K;
+    real* __restrict__ Vw = (real*)g.V;
+    if (PREC == kPrecFP64) {
+        const double* __restrict__ Yr = g.Y64 + buf * NP1;
+#pragma unroll 2
+        for (int j = j0; j < R; j += stride) {
+            const ushort4 rs = rspec[j];
+            double k = (double)Kz[j];
+            if (poly == 2 || poly == 5)
+                k *= exp_neg_small((double)cexp[j] * s, poly);
+            else if (poly == 9)
+                k *= exp(-(double)cexp[j] * s);
+            const double ya = Yr[rs.x];
+            if (j < R1) {
+                Vw[j] = (real)(k * ya);
+                Vw[rs.w] = (real)k;
+            } else if (j < R12) {
+                const double yb = Yr[rs.y];
+                Vw[j] = (real)(k * ya * yb);
+                Vw[rs.w] = (real)(k * yb);
+                Vw[rs.w + 1] = (real)(k * ya);
+            } else {
+                const double yb = Yr[rs.y], yc = Yr[rs.z];
+                const double ka = k * ya;
+                Vw[j] = (real)(ka * yb * yc);
+                Vw[rs.w] = (real)(k * yb * yc);
+                Vw[rs.w + 1] = (real)(ka * yc);
+                Vw[rs.w + 2] = (real)(ka * yb);
+            }
+        }
+    } else {
+        const float* __restrict__ Yc32 = g.Y32 + buf * NP1;
+        const bool varying = !constant;
+#pragma unroll 2
+        for (int j = j0; j < R; j += stride) {
+            const ushort4 rs = rspec[j];
+            float k = (float)Kz[j];
+            if (varying) k = __fmul_rn(k, ex2_approx(-__fmul_rn((float)cexp[j], u)));
+            const float ya = Yc32[rs.x];
+            if (j < R1) {
+                Vw[j] = (real)__fmul_rn(k, ya);
+                Vw[rs.w] = (real)k;
+            } else if (j < R12) {
+                const float yb = Yc32[rs.y];
+                Vw[j] = (real)__fmul_rn(__fmul_rn(k, ya), yb);
+                Vw[rs.w] = (real)__fmul_rn(k, yb);
+                Vw[rs.w + 1] = (real)__fmul_rn(k, ya);
+            } else {
+                const float yb = Yc32[rs.y], yc = Yc32[rs.z];
+                const float ka = __fmul_rn(k, ya);
+                Vw[j] = (real)__fmul_rn(__fmul_rn(ka, yb), yc);
+                Vw[rs.w] = (real)__fmul_rn(__fmul_rn(k, yb), yc);
+                Vw[rs.w + 1] = (real)__fmul_rn(ka, yc);
+                Vw[rs.w + 2] = (real)__fmul_rn(ka, yb);
+            }
+        }
+    }
+}
+
 template <int PREC, bool FEAT>
 __device__ void run_group(const PlanDev& P, const OptsDev& O, const unsigned char* tb, const unsigned char* mlp_smem,
                           unsigned char* gbase, const int lane, const GroupSync gs) {
@@ -395,8 +498,6 @@ __device__ void run_group(const PlanDev& P, const OptsDev& O, const unsigned cha
     g.feat = (float*)(gbase + P.gl.off_feat);
     g.hist = (int*)(g.feat + 384);
 
-    const ushort4* __restrict__ rspec = g.rspec;
-    const real* __restrict__ cexp = (const real*)g.cexp;
     const uint32_t* __restrict__ terms = g.terms;
     const ushort4* __restrict__ fix = g.fix;
     real* V = (real*)g.V;
@@ -491,76 +592,19 @@ __device__ void run_group(const PlanDev& P, const OptsDev& O, const unsigned cha
         gs.sync();
 
         // ---- step loop (Sec. 4: adaptive network timesteps) ----
+        // have_a: phase (a) of the current state was already computed, by the
+        // speculative pass that overlapped the previous decision
+        bool have_a = false;
+        const bool spec = G >= 64 && PREC == kPrecMixed;
         while (!S.done) {
             const int cur = S.cur, nxt = cur ^ 1;
-            const double* Yc = Y64 + cur * NP1;
 
             if (!S.rhs_valid) {
-                // (a) rates k_j(t), fluxes f_j and reactant-slot partials (Eq. 1),
-                //     reactions sorted 1-, 2-, 3-body: no multiply by a missing reactant
-                if (PREC == kPrecFP64) {
-                    const int poly = S.poly;
-                    const double s = S.s;
-                    const double* __restrict__ Yr = Yc;
-                    const real* __restrict__ Kz = K;
-                    real* __restrict__ Vw = V;
-#pragma unroll 2
-                    for (int j = lane; j < R; j += G) {
-                        const ushort4 rs = rspec[j];
-                        double k = (double)Kz[j];
-                        if (poly == 2 || poly == 5)
-                            k *= exp_neg_small((double)cexp[j] * s, poly);
-                        else if (poly == 9)
-                            k *= exp(-(double)cexp[j] * s);
-                        const double ya = Yr[rs.x];
-                        if (j < R1) {
-                            Vw[j] = (real)(k * ya);
-                            Vw[rs.w] = (real)k;
-                        } else if (j < R12) {
-                            const double yb = Yr[rs.y];
-                            Vw[j] = (real)(k * ya * yb);
-                            Vw[rs.w] = (real)(k * yb);
-                            Vw[rs.w + 1] = (real)(k * ya);
-                        } else {
-                            const double yb = Yr[rs.y], yc = Yr[rs.z];
-                            const double ka = k * ya;
-                            Vw[j] = (real)(ka * yb * yc);
-                            Vw[rs.w] = (real)(k * yb * yc);
-                            Vw[rs.w + 1] = (real)(ka * yc);
-                            Vw[rs.w + 2] = (real)(ka * yb);
-                        }
-                    }
-                } else {
-                    const float* __restrict__ Yc32 = Y32 + cur * NP1;
-                    const real* __restrict__ Kz = K;
-                    real* __restrict__ Vw = V;
-                    const float u = S.u;
-                    const bool varying = !S.constant;
-#pragma unroll 2
-                    for (int j = lane; j < R; j += G) {
-                        const ushort4 rs = rspec[j];
-                        float k = (float)Kz[j];
-                        if (varying) k = __fmul_rn(k, ex2_approx(-__fmul_rn((float)cexp[j], u)));
-                        const float ya = Yc32[rs.x];
-                        if (j < R1) {
-                            Vw[j] = (real)__fmul_rn(k, ya);
-                            Vw[rs.w] = (real)k;
-                        } else if (j < R12) {
-                            const float yb = Yc32[rs.y];
-                            Vw[j] = (real)__fmul_rn(__fmul_rn(k, ya), yb);
-                            Vw[rs.w] = (real)__fmul_rn(k, yb);
-                            Vw[rs.w + 1] = (real)__fmul_rn(k, ya);
-                        } else {
-                            const float yb = Yc32[rs.y], yc = Yc32[rs.z];
-                            const float ka = __fmul_rn(k, ya);
-                            Vw[j] = (real)__fmul_rn(__fmul_rn(ka, yb), yc);
-                            Vw[rs.w] = (real)__fmul_rn(__fmul_rn(k, yb), yc);
-                            Vw[rs.w + 1] = (real)__fmul_rn(ka, yc);
-                            Vw[rs.w + 2] = (real)__fmul_rn(ka, yb);
-                        }
-                    }
+                if (!have_a) {
+                    // (a) rates, fluxes and reactant-slot partials at this state
+                    flux_pass<PREC>(P, g, lane, G, cur, S.constant, S.s, S.u, S.poly);
+                    gs.sync();
                 }
-                gs.sync();
                 // (b) balanced gathers: chunk `lane` of the flat term list; the
                 //     next two terms are loaded ahead of the current one's store
                 if (lane < Q) {
@@ -689,8 +733,28 @@ __device__ void run_group(const PlanDev& P, const OptsDev& O, const unsigned cha
             }
 
             // (d) update and error measures, then (e) the decision (lane 0)
-            update_reduce<PREC>(P, O, g, lane, cur, S.h, z);
+            // while warps 1.. compute (a) for the candidate state at t + h,
+            // as the next step needs it if this one is accepted
+            const double h_now = S.h;
+            if (spec && lane == 32) {
+                // the candidate state's profile factor, once per group (FP64 is scarce)
+                if (!S.constant) {
+                    const double s_spec = (S.t + h_now) * S.inv_tau;
+                    const double xm = P.cmax * s_spec;
+                    S.s_spec = s_spec;
+                    S.u_spec = (float)(s_spec * 1.4426950408889634);
+                    S.poly_spec = xm <= 1e-6 ? 2 : (xm <= 0.0009765625 ? 5 : 9);
+                } else {
+                    S.s_spec = 0.0;
+                    S.u_spec = 0.f;
+                    S.poly_spec = 0;
+                }
+            }
+            update_reduce<PREC>(P, O, g, lane, cur, h_now, z);
             gs.sync();
+            if (spec && lane >= 32)
+                flux_pass<PREC>(P, g, lane - 32, G - 32, nxt, S.constant, S.s_spec, S.u_spec, S.poly_spec);
+            have_a = spec;
             if (lane == 0) {
                 const Verdict v = combine<PREC>(P, O, g);
                 const double h = S.h;

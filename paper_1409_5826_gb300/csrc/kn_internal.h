@@ -78,7 +78,10 @@ struct GroupState {
     int fresh;         // current state was reached by an accepted step: features due
     int mlp_try;       // the current attempt uses the learned proposal
     int found;         // label search: a grid step passed
-    int pad3;
+    int poly_spec;     // the speculative pass's series choice ...
+    double s_spec;     // ... t/tau of the candidate state ...
+    float u_spec;      // ... and t/(tau ln 2)
+    float pad3;
 };
 
 struct PlanDev {
@@ -143,6 +146,8 @@ struct OptsDev {
     const void* mlpW;
     const float* mlpNorm;
     float mlp_margin;  // the proposal uses e^(out - margin)
+    // FP32 guard band of the mixed form's accept test (see update_reduce)
+    float eps_r32, ymin_lo32, ymin_hi32, band_lo32, band_hi32, kappa32;
     int learn;   // 1: propose with the network
     int record;  // 1: write (features, label) at every accepted state
     int mlp_smem_off;  // byte offset of the staged network in the CTA's shared memory
