@@ -171,7 +171,7 @@ static kn_status build_tables(kn_network* n, int prec, int Q, Tables& T) {
     TableLayout tl{};
     int off = 0;
     tl.off_A = off;
-    off = pad16(off + 8 * N);
+    off = pad16(off + real * N);
     tl.off_rspec = off;
     off = pad16(off + 8 * R);
     tl.off_cexp = off;
@@ -182,7 +182,14 @@ static kn_status build_tables(kn_network* n, int prec, int Q, Tables& T) {
     off = pad16(off + 2 * (int)fix.size());
     tl.bytes = off;
     std::vector<unsigned char> blob(off, 0);
-    memcpy(blob.data() + tl.off_A, n->A.data(), 8 * N);
+    for (int i = 0; i < N; ++i) {
+        if (prec == kPrecFP64) {
+            memcpy(blob.data() + tl.off_A + 8 * i, &n->A[i], 8);
+        } else {
+            const float af = (float)n->A[i];
+            memcpy(blob.data() + tl.off_A + 4 * i, &af, 4);
+        }
+    }
     for (int jn = 0; jn < R; ++jn) {
         const int j = n->perm[jn];
         uint16_t rs[4];
@@ -232,8 +239,8 @@ static GroupLayout group_layout(const kn_network* n, int prec, int G, bool feat)
     off = pad16(off + real * (n->R + n->S_r + 1));
     g.off_K = off;
     off = pad16(off + real * n->R);
-    g.off_Y64 = off;
-    off = pad16(off + 8 * 2 * (n->N + 1));
+    g.off_Y = off;
+    off = pad16(off + (prec == kPrecFP64 ? 8 : 4) * 2 * (n->N + 1));
     g.off_Y32 = off;
     if (prec == kPrecMixed) off = pad16(off + 4 * 2 * (n->N + 1));
     g.off_Fk = off;
@@ -241,7 +248,7 @@ static GroupLayout group_layout(const kn_network* n, int prec, int G, bool feat)
     g.off_carry = off;
     off = pad16(off + 8 * 2 * G);
     g.off_red = off;
-    off = pad16(off + 32 * (8 * 3 + 4 + 4));
+    off = pad16(off + (G / 32) * (8 * 3 + 4 + 4));
     g.off_feat = off;
     if (feat) off = pad16(off + 4 * 384 + 4 * (3 * 64 + 4));
     g.off_state = off;
@@ -572,6 +579,10 @@ static void set_guard_band(OptsDev& D, const kn_opts* o) {
     const double band = 8.0 * (2.0 * u / o->eps_r + 4.0 * u);
     D.eps_r32 = (float)o->eps_r;
     D.kappa32 = (float)o->kappa;
+    D.eps_c32 = (float)o->eps_c;
+    D.ga32 = (float)(o->safety * o->eps_r);
+    D.gb32 = (float)(o->safety * o->eps_c);
+    D.grow32 = (float)o->grow_max;
     D.band_lo32 = (float)(1.0 - band);
     D.band_hi32 = (float)(1.0 + band);
     D.ymin_lo32 = (float)(o->y_min * (1.0 - 8.0 * u));

@@ -120,7 +120,7 @@ __device__ __forceinline__ void leader_prepare(GroupState& S, const PlanDev& P, 
         const double s = S.t * S.inv_tau;
         S.s = s;
         if (PREC == kPrecMixed) {
-            S.u = (float)(s * 1.4426950408889634);
+            S.u = __fmul_rn(__double2float_rn(S.t), S.u_scale);
         } else {
             const double xm = P.cmax * s;
             S.poly = xm <= 1e-6 ? 2 : (xm <= 0.0009765625 ? 5 : 9);
@@ -132,7 +132,7 @@ __device__ __forceinline__ void leader_prepare(GroupState& S, const PlanDev& P, 
 // one zone group: fetch zones until the queue is empty
 // ---------------------------------------------------------------------------
 struct GroupPtrs {
-    const double* A;
+    const void* A;  // real[N]
     const ushort4* rspec;
     const void* cexp;
     const uint32_t* terms;
@@ -140,7 +140,8 @@ struct GroupPtrs {
     unsigned char* gbase;
     void* V;
     void* K;
-    double* Y64;
+    double* Y64;  // FP64 form: the abundances
+    float* Ylo;   // mixed form: low parts of the float-float abundances (high parts: Y32)
     float* Y32;
     void* Fk;
     double* red_c;
@@ -154,69 +155,24 @@ struct GroupPtrs {
 
 // (d) kappa-switched update (Sec. 3, Eq. 3) with step h from buffer cur into
 // nxt, and each warp's share of the error measures (no barrier inside).
-template <int PREC>
-__device__ __forceinline__ void update_reduce(const PlanDev& P, const OptsDev& O, const GroupPtrs& g, int lane,
-                                              int cur, double h, int z) {
-    using real = typename PrecTraits<PREC>::real;
+// FP64 form: every step in FP64, in the order of the definitions.
+__device__ __forceinline__ void update_reduce_fp64(const PlanDev& P, const OptsDev& O, const GroupPtrs& g, int lane,
+                                                   int cur, double h, int z) {
     const int N = P.N, G = P.G, NP1 = N + 1;
-    const real* Fk = (const real*)g.Fk;
+    const double* Fk = (const double*)g.Fk;
+    const double* A = (const double*)g.A;
     const double* Yc = g.Y64 + cur * NP1;
     double* Yn64 = g.Y64 + (cur ^ 1) * NP1;
-    float* Yn32 = g.Y32 + (cur ^ 1) * NP1;
-    const float* Yc32 = g.Y32 + cur * NP1;
-    const double kappa = O.kappa, ymin = O.y_min, eps_r = O.eps_r;
-    [[maybe_unused]] const float h32 = PREC == kPrecMixed ? (float)h : 0.f;
+    const double kappa = O.kappa, ymin = O.y_min;
     double csum = 0.0, bn = 0.0, bd = 1.0;
-    float rmax = 0.f;
-    int ok = 1;
     for (int i = lane; i < N; i += G) {
-        const double y = Yc[i];
-        double yn;
-        float yn32 = 0.f, y32 = 0.f;
-        if (PREC == kPrecMixed) {
-            // Eq. 3 in FP32, the precision F+ and k arrive in: on the
-            // asymptotic branch y' itself (relative accuracy, positivity), on
-            // the explicit branch the change dt (F+ - k y), added to the FP64
-            // abundance so that small changes accumulate without loss.
-            const float fp32 = Fk[i], kk32 = Fk[N + i];
-            y32 = Yc32[i];
-            const float kdt32 = kk32 * h32;
-            const bool asym = kdt32 >= O.kappa32;
-            const float v = asym ? __fdiv_rn(fmaf(h32, fp32, y32), 1.f + kdt32) : h32 * fmaf(-kk32, y32, fp32);
-            const double v64 = (double)v;
-            yn = asym ? v64 : y + v64;
-            yn32 = asym ? v : (float)yn;
-            Yn32[i] = yn32;
-        } else {
-            const double fp = (double)Fk[i], kk = (double)Fk[N + i];
-            const double kdt = kk * h;
-            yn = (kdt >= kappa) ? (y + h * fp) / (1.0 + kdt) : y + h * (fp - kk * y);
-        }
+        const double y = Yc[i], fp = Fk[i], kk = Fk[N + i];
+        const double kdt = kk * h;
+        const double yn = (kdt >= kappa) ? (y + h * fp) / (1.0 + kdt) : y + h * (fp - kk * y);
         Yn64[i] = yn;
         const double d = yn - y;
-        csum = fma(g.A[i], d, csum);
-        if (PREC == kPrecMixed) {
-            // The accept test's decisions are those of the FP64 compares
-            // m > y_min and |d| <= eps_r m; they are taken on the FP32 copies
-            // when the FP32 values lie clearly on one side (outside a guard
-            // band that bounds the FP32 rounding of y, y', d and m), and in
-            // FP64 inside the band.
-            const float m32 = fmaxf(y32, yn32);
-            int tested;
-            if (m32 > O.ymin_hi32) tested = 1;
-            else if (m32 < O.ymin_lo32) tested = 0;
-            else tested = (y > yn ? y : yn) > ymin;
-            if (tested) {
-                const float d32 = fabsf(yn32 - y32);
-                const float lim = O.eps_r32 * m32;
-                int pass_i;
-                if (d32 < __fmul_rn(lim, O.band_lo32)) pass_i = 1;
-                else if (d32 > __fmul_rn(lim, O.band_hi32)) pass_i = 0;
-                else pass_i = fabs(d) <= eps_r * (y > yn ? y : yn);
-                ok &= pass_i;
-                rmax = fmaxf(rmax, __fdividef(d32, m32));  // the dt proposal, FP32
-            }
-        } else if ((y > yn ? y : yn) > ymin) {
+        csum = fma(A[i], d, csum);
+        if ((y > yn ? y : yn) > ymin) {
             const double m = y > yn ? y : yn;
             const double ad = fabs(d);
             if (ad * bd > bn * m) {
@@ -225,34 +181,140 @@ __device__ __forceinline__ void update_reduce(const PlanDev& P, const OptsDev& O
             }
         }
         if (O.probe) {
-            O.probe_Fp[(size_t)z * N + i] = (double)Fk[i];
-            O.probe_k[(size_t)z * N + i] = (double)Fk[N + i];
+            O.probe_Fp[(size_t)z * N + i] = fp;
+            O.probe_k[(size_t)z * N + i] = kk;
             O.probe_Y1[(size_t)z * N + i] = yn;
         }
     }
 #pragma unroll
     for (int off = 16; off > 0; off >>= 1) {
         csum += __shfl_xor_sync(0xffffffffu, csum, off);
-        if (PREC == kPrecMixed) {
-            rmax = fmaxf(rmax, __shfl_xor_sync(0xffffffffu, rmax, off));
-        } else {
-            const double on = __shfl_xor_sync(0xffffffffu, bn, off);
-            const double od = __shfl_xor_sync(0xffffffffu, bd, off);
-            if (on * bd > bn * od) {
-                bn = on;
-                bd = od;
-            }
+        const double on = __shfl_xor_sync(0xffffffffu, bn, off);
+        const double od = __shfl_xor_sync(0xffffffffu, bd, off);
+        if (on * bd > bn * od) {
+            bn = on;
+            bd = od;
         }
     }
-    ok = __all_sync(0xffffffffu, ok);
     if ((lane & 31) == 0) {
         const int w = lane >> 5;
         g.red_c[w] = csum;
         g.red_n[w] = bn;
         g.red_d[w] = bd;
+    }
+}
+
+// Knuth's TwoSum (TAOCP vol. 2, 4.2.2): s = fl(a + b) and the exact rounding
+// error e = (a + b) - s, for any a, b (no ordering condition).
+__device__ __forceinline__ void two_sum(float a, float b, float& s, float& e) {
+    s = __fadd_rn(a, b);
+    const float bv = __fsub_rn(s, a);
+    const float av = __fsub_rn(s, bv);
+    e = __fadd_rn(__fsub_rn(a, av), __fsub_rn(b, bv));
+}
+
+// Mixed form.  The abundances are float-float pairs y = yh + yl (|yl| at most
+// half an ulp of yh, so yh is the FP32 copy the flux pass reads; about 48
+// significant bits), and the update runs in FP32, the precision F+ and k
+// arrive in: on the asymptotic branch y' itself (relative accuracy,
+// positivity), on the explicit branch the change dt (F+ - k y), added to the
+// pair exactly up to one rounding of the low part.  The conservation sum
+// sum A (y' - y) is a float-float sum of exact products, so it resolves the
+// stored change far below eps_c; no FP64 instruction runs per species.
+__device__ __forceinline__ void update_reduce_mixed(const PlanDev& P, const OptsDev& O, const GroupPtrs& g, int lane,
+                                                    int cur, double h, int z) {
+    const int N = P.N, G = P.G, NP1 = N + 1;
+    const float* Fk = (const float*)g.Fk;
+    const float* A = (const float*)g.A;
+    const float* Yh = g.Y32 + cur * NP1;
+    const float* Yl = g.Ylo + cur * NP1;
+    float* Nh = g.Y32 + (cur ^ 1) * NP1;
+    float* Nl = g.Ylo + (cur ^ 1) * NP1;
+    const float h32 = (float)h;
+    float cs_h = 0.f, cs_l = 0.f, rmax = 0.f;
+    int ok = 1;
+    for (int i = lane; i < N; i += G) {
+        const float yh = Yh[i], yl = Yl[i], fp = Fk[i], kk = Fk[N + i];
+        const float kdt = __fmul_rn(kk, h32);
+        float nh, nl, dh, dl;
+        if (kdt >= O.kappa32) {
+            nh = __fdiv_rn(fmaf(h32, fp, yh), __fadd_rn(1.f, kdt));
+            nl = 0.f;
+            two_sum(nh, -yh, dh, dl);
+            dl = __fsub_rn(dl, yl);
+        } else {
+            dh = __fmul_rn(h32, fmaf(-kk, yh, fp));
+            dl = 0.f;
+            float s, e;
+            two_sum(yh, dh, s, e);
+            two_sum(s, __fadd_rn(e, yl), nh, nl);
+        }
+        Nh[i] = nh;
+        Nl[i] = nl;
+        // A (dh + dl): the product a dh split exactly by an FMA
+        const float a = A[i];
+        const float p = __fmul_rn(a, dh);
+        const float pe = fmaf(a, dh, -p);
+        float s, e;
+        two_sum(cs_h, p, s, e);
+        cs_h = s;
+        cs_l = __fadd_rn(cs_l, __fadd_rn(e, fmaf(a, dl, pe)));
+        // The accept test's decisions are those of the compares m > y_min
+        // and |d| <= eps_r m on the pairs; they are taken on the high parts
+        // when those lie clearly on one side (outside a guard band that
+        // bounds their rounding), and on the pairs in FP64 inside the band.
+        const float m32 = fmaxf(yh, nh);
+        int tested;
+        if (m32 > O.ymin_hi32) tested = 1;
+        else if (m32 < O.ymin_lo32) tested = 0;
+        else tested = fmax((double)yh + (double)yl, (double)nh + (double)nl) > O.y_min;
+        if (tested) {
+            const float d32 = fabsf(__fsub_rn(nh, yh));
+            const float lim = __fmul_rn(O.eps_r32, m32);
+            int pass_i;
+            if (d32 < __fmul_rn(lim, O.band_lo32)) {
+                pass_i = 1;
+            } else if (d32 > __fmul_rn(lim, O.band_hi32)) {
+                pass_i = 0;
+            } else {
+                const double y = (double)yh + (double)yl, yn = (double)nh + (double)nl;
+                pass_i = fabs(yn - y) <= O.eps_r * (y > yn ? y : yn);
+            }
+            ok &= pass_i;
+            rmax = fmaxf(rmax, __fdividef(d32, m32));  // the dt proposal, FP32
+        }
+        if (O.probe) {
+            O.probe_Fp[(size_t)z * N + i] = (double)fp;
+            O.probe_k[(size_t)z * N + i] = (double)kk;
+            O.probe_Y1[(size_t)z * N + i] = (double)nh + (double)nl;
+        }
+    }
+#pragma unroll
+    for (int off = 16; off > 0; off >>= 1) {
+        const float oh = __shfl_xor_sync(0xffffffffu, cs_h, off);
+        const float ol = __shfl_xor_sync(0xffffffffu, cs_l, off);
+        float s, e;
+        two_sum(cs_h, oh, s, e);
+        cs_h = s;
+        cs_l = __fadd_rn(__fadd_rn(cs_l, ol), e);
+        rmax = fmaxf(rmax, __shfl_xor_sync(0xffffffffu, rmax, off));
+    }
+    ok = __all_sync(0xffffffffu, ok);
+    if ((lane & 31) == 0) {
+        const int w = lane >> 5;
+        ((float2*)g.red_c)[w] = make_float2(cs_h, cs_l);
         g.red_r[w] = rmax;
         g.red_f[w] = ok;
     }
+}
+
+template <int PREC>
+__device__ __forceinline__ void update_reduce(const PlanDev& P, const OptsDev& O, const GroupPtrs& g, int lane,
+                                              int cur, double h, int z) {
+    if (PREC == kPrecMixed)
+        update_reduce_mixed(P, O, g, lane, cur, h, z);
+    else
+        update_reduce_fp64(P, O, g, lane, cur, h, z);
 }
 
 // lane 0, after the barrier that follows update_reduce: combine the warps.
@@ -260,32 +322,43 @@ __device__ __forceinline__ void update_reduce(const PlanDev& P, const OptsDev& O
 // finiteness test reads that sum.
 struct Verdict {
     double cons, bn, bd;
-    float rmax;
+    float rmax, cons32;
     int fin, pass;
 };
 template <int PREC>
 __device__ __forceinline__ Verdict combine(const PlanDev& P, const OptsDev& O, const GroupPtrs& g) {
     const int nw = P.G >> 5;
-    Verdict v{0.0, 0.0, 1.0, 0.f, 1, 0};
-    double cs = 0.0;
-    int ok = 1;
-    for (int w = 0; w < nw; ++w) {
-        cs += g.red_c[w];
-        if (PREC == kPrecMixed) {
+    Verdict v{0.0, 0.0, 1.0, 0.f, 0.f, 1, 0};
+    if (PREC == kPrecMixed) {
+        float ch = 0.f, cl = 0.f;
+        int ok = 1;
+        for (int w = 0; w < nw; ++w) {
+            const float2 c = ((const float2*)g.red_c)[w];
+            float s, e;
+            two_sum(ch, c.x, s, e);
+            ch = s;
+            cl = __fadd_rn(__fadd_rn(cl, c.y), e);
             v.rmax = fmaxf(v.rmax, g.red_r[w]);
-        } else {
+            ok &= g.red_f[w];
+        }
+        const float cs = __fadd_rn(ch, cl);
+        v.fin = isfinite(cs) ? 1 : 0;
+        v.cons32 = fabsf(cs);
+        v.pass = v.fin && ok && v.cons32 <= O.eps_c32;
+    } else {
+        double cs = 0.0;
+        for (int w = 0; w < nw; ++w) {
+            cs += g.red_c[w];
             const double on = g.red_n[w], od = g.red_d[w];
             if (on * v.bd > v.bn * od) {
                 v.bn = on;
                 v.bd = od;
             }
         }
-        ok &= g.red_f[w];
+        v.fin = isfinite(cs) ? 1 : 0;
+        v.cons = fabs(cs);
+        v.pass = v.fin && v.cons <= O.eps_c && v.bn <= O.eps_r * v.bd;
     }
-    v.fin = isfinite(cs) ? 1 : 0;
-    v.cons = fabs(cs);
-    v.pass = PREC == kPrecMixed ? (v.fin && ok && v.cons <= O.eps_c)
-                                : (v.fin && v.cons <= O.eps_c && v.bn <= O.eps_r * v.bd);
     return v;
 }
 
@@ -479,7 +552,7 @@ __device__ void run_group(const PlanDev& P, const OptsDev& O, const unsigned cha
     const bool feats_on = FEAT && (O.learn || O.record);
 
     GroupPtrs g;
-    g.A = (const double*)(tb + P.tl.off_A);
+    g.A = tb + P.tl.off_A;
     g.rspec = (const ushort4*)(tb + P.tl.off_rspec);
     g.cexp = tb + P.tl.off_cexp;
     g.terms = (const uint32_t*)(tb + P.tl.off_terms);
@@ -487,14 +560,18 @@ __device__ void run_group(const PlanDev& P, const OptsDev& O, const unsigned cha
     g.gbase = gbase;
     g.V = gbase + P.gl.off_V;
     g.K = gbase + P.gl.off_K;
-    g.Y64 = (double*)(gbase + P.gl.off_Y64);
+    g.Y64 = (double*)(gbase + P.gl.off_Y);
+    g.Ylo = (float*)(gbase + P.gl.off_Y);
     g.Y32 = (float*)(gbase + P.gl.off_Y32);
     g.Fk = gbase + P.gl.off_Fk;
-    g.red_c = (double*)(gbase + P.gl.off_red);
-    g.red_n = g.red_c + 32;
-    g.red_d = g.red_n + 32;
-    g.red_r = (float*)(g.red_d + 32);
-    g.red_f = (int*)(g.red_r + 32);
+    {
+        const int nw = G >> 5;
+        g.red_c = (double*)(gbase + P.gl.off_red);
+        g.red_n = g.red_c + nw;
+        g.red_d = g.red_n + nw;
+        g.red_r = (float*)(g.red_d + nw);
+        g.red_f = (int*)(g.red_r + nw);
+    }
     g.feat = (float*)(gbase + P.gl.off_feat);
     g.hist = (int*)(g.feat + 384);
 
@@ -503,6 +580,7 @@ __device__ void run_group(const PlanDev& P, const OptsDev& O, const unsigned cha
     real* V = (real*)g.V;
     real* K = (real*)g.K;
     double* Y64 = g.Y64;
+    float* Ylo = g.Ylo;
     float* Y32 = g.Y32;
     real* Fk = (real*)g.Fk;
     GroupState& S = *(GroupState*)(gbase + P.gl.off_state);
@@ -525,16 +603,24 @@ __device__ void run_group(const PlanDev& P, const OptsDev& O, const unsigned cha
             int bad = 0;
             for (int i = lane; i < N; i += G) {
                 const double y = Yg[i];
-                Y64[i] = y;
-                if (PREC == kPrecMixed) Y32[i] = (float)y;
+                if (PREC == kPrecMixed) {
+                    const float hi = __double2float_rn(y);
+                    Y32[i] = hi;
+                    Ylo[i] = __double2float_rn(y - (double)hi);
+                } else {
+                    Y64[i] = y;
+                }
                 bad |= !(isfinite(y) && y >= 0.0);
             }
             if (lane == 0) {
-                Y64[N] = 1.0;
-                Y64[NP1 + N] = 1.0;
                 if (PREC == kPrecMixed) {
                     Y32[N] = 1.0f;
                     Y32[NP1 + N] = 1.0f;
+                    Ylo[N] = 0.0f;
+                    Ylo[NP1 + N] = 0.0f;
+                } else {
+                    Y64[N] = 1.0;
+                    Y64[NP1 + N] = 1.0;
                 }
                 const double T0 = P.T0[z], rho0 = P.rho0[z], tau = P.tau[z];
                 const double ts = P.t_start[z], te = P.t_end[z], dtt = P.dt_trial[z];
@@ -546,6 +632,7 @@ __device__ void run_group(const PlanDev& P, const OptsDev& O, const unsigned cha
                 S.dt = dtt > 0.0 ? dtt : ts;
                 S.constant = !(tau > 0.0);
                 S.inv_tau = S.constant ? 0.0 : 1.0 / tau;
+                S.u_scale = S.constant ? 0.f : __double2float_rn(S.inv_tau * 1.4426950408889634);
                 S.s = 0.0;
                 S.poly = 0;
                 S.u = 0.f;
@@ -737,29 +824,19 @@ __device__ void run_group(const PlanDev& P, const OptsDev& O, const unsigned cha
             // as the next step needs it if this one is accepted
             const double h_now = S.h;
             if (spec && lane == 32) {
-                // the candidate state's profile factor, once per group (FP64 is scarce)
-                if (!S.constant) {
-                    const double s_spec = (S.t + h_now) * S.inv_tau;
-                    const double xm = P.cmax * s_spec;
-                    S.s_spec = s_spec;
-                    S.u_spec = (float)(s_spec * 1.4426950408889634);
-                    S.poly_spec = xm <= 1e-6 ? 2 : (xm <= 0.0009765625 ? 5 : 9);
-                } else {
-                    S.s_spec = 0.0;
-                    S.u_spec = 0.f;
-                    S.poly_spec = 0;
-                }
+                // the candidate state's profile factor (t + h) / (tau ln 2), once per group
+                S.u_spec = S.constant ? 0.f : __fmul_rn(__double2float_rn(S.t + h_now), S.u_scale);
             }
             update_reduce<PREC>(P, O, g, lane, cur, h_now, z);
             gs.sync();
             if (spec && lane >= 32)
-                flux_pass<PREC>(P, g, lane - 32, G - 32, nxt, S.constant, S.s_spec, S.u_spec, S.poly_spec);
+                flux_pass<PREC>(P, g, lane - 32, G - 32, nxt, S.constant, 0.0, S.u_spec, 0);
             have_a = spec;
             if (lane == 0) {
                 const Verdict v = combine<PREC>(P, O, g);
                 const double h = S.h;
                 if (O.probe) {
-                    O.probe_cons[z] = v.cons;
+                    O.probe_cons[z] = PREC == kPrecMixed ? (double)v.cons32 : v.cons;
                     O.probe_rel[z] = PREC == kPrecMixed ? (double)v.rmax : v.bn / v.bd;
                     S.done = 1;
                 } else if (O.replay_dt || v.pass) {
@@ -784,12 +861,10 @@ __device__ void run_group(const PlanDev& P, const OptsDev& O, const unsigned cha
                         if (gb < gfac) gfac = gb;
                         S.dt = h * gfac;
                     } else {
-                        // mixed form: the accept test above is FP64; the growth
-                        // factor is proposed in FP32
-                        float gfac = (float)O.grow_max;
-                        const float ga = __fdiv_rn((float)(O.safety * O.eps_r), fmaxf(v.rmax, 1e-30f));
-                        const float gb = __fdiv_rn((float)(O.safety * O.eps_c), fmaxf((float)v.cons, 1e-30f));
-                        gfac = fminf(gfac, fminf(ga, gb));
+                        // mixed form: the growth factor in FP32
+                        const float ga = __fdiv_rn(O.ga32, fmaxf(v.rmax, 1e-30f));
+                        const float gb = __fdiv_rn(O.gb32, fmaxf(v.cons32, 1e-30f));
+                        const float gfac = fminf(O.grow32, fminf(ga, gb));
                         S.dt = h * (double)gfac;
                     }
                     S.dt_plain = S.dt;
@@ -819,13 +894,23 @@ __device__ void run_group(const PlanDev& P, const OptsDev& O, const unsigned cha
 
         // ---- write back (Sec. 6 step 3 outputs: abundances, energy, final dt) ----
         if (!O.probe) {
-            const double* Yc = Y64 + S.cur * NP1;
             double* Yg = P.Y + (size_t)z * N;
             double e = 0.0;
             if (S.status != 5) {
                 for (int i = lane; i < N; i += G) {
-                    if (P.bind) e = fma(P.bind[i], Yc[i] - Yg[i], e);  // Yg still holds Y(t_start)
-                    Yg[i] = Yc[i];
+                    const double y0 = Yg[i];  // still Y(t_start)
+                    double y;
+                    if (PREC == kPrecMixed) {
+                        // a pair that never changed returns the FP64 input bit for bit
+                        const float hi = Y32[S.cur * NP1 + i], lo = Ylo[S.cur * NP1 + i];
+                        const float hi0 = __double2float_rn(y0);
+                        const float lo0 = __double2float_rn(y0 - (double)hi0);
+                        y = (hi == hi0 && lo == lo0) ? y0 : (double)hi + (double)lo;
+                    } else {
+                        y = Y64[S.cur * NP1 + i];
+                    }
+                    if (P.bind) e = fma(P.bind[i], y - y0, e);
+                    Yg[i] = y;
                 }
             }
             if (P.bind) {

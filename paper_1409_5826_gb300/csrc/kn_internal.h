@@ -37,7 +37,7 @@ constexpr int kMlpSmemBytes = (kMlpFeatures * kMlpHidden + kMlpHidden * kMlpHidd
 // that the flux loop is warp-uniform and multiplies by no sentinel.
 struct TableLayout {
     int32_t bytes;        // total (multiple of 16)
-    int32_t off_A;        // double[N]
+    int32_t off_A;        // real[N] (mass numbers; integers, exact in FP32)
     int32_t off_rspec;    // ushort4[R]: reactant species a, b, c (N = none), V index of slot 0
     int32_t off_cexp;     // real[R]: c_j = n_j + 3 (r_j - 1), so that along the profile
                           //   k_j(t) = k_j(T0, rho0) exp(-c_j t / tau)
@@ -50,11 +50,12 @@ struct GroupLayout {
     int32_t bytes;
     int32_t off_V;      // real[R + S_r + 1]: fluxes, reactant-slot partials, constant 0
     int32_t off_K;      // real[R]: the zone's rates at (T0, rho0)
-    int32_t off_Y64;    // double[2][N + 1]; entry N is the constant 1
-    int32_t off_Y32;    // float[2][N + 1] (mixed only)
+    int32_t off_Y;      // FP64: double[2][N + 1], entry N the constant 1; mixed: float[2][N + 1],
+                        //   the low parts of the float-float abundances (0 at entry N)
+    int32_t off_Y32;    // float[2][N + 1] (mixed only): the high parts, entry N the constant 1
     int32_t off_Fk;     // real[2N]: F+ then k (mixed: Kahan sums rounded to float)
     int32_t off_carry;  // FP64: double[2][Q]; mixed: float2[2][Q] Kahan (sum, compensation)
-    int32_t off_red;    // per-warp reduction scratch: double[32] x 3, float[32], int[32]
+    int32_t off_red;    // per-warp reduction scratch, W = G/32 warps: double[W] x 3, float[W], int[W]
     int32_t off_feat;   // learned proposal / records: float[64 feats, 64 inputs, 128 h1, 128 h2],
                         //   int[3][64] histograms + 4 counters (absent when unused)
     int32_t off_state;  // GroupState
@@ -78,10 +79,8 @@ struct GroupState {
     int fresh;         // current state was reached by an accepted step: features due
     int mlp_try;       // the current attempt uses the learned proposal
     int found;         // label search: a grid step passed
-    int poly_spec;     // the speculative pass's series choice ...
-    double s_spec;     // ... t/tau of the candidate state ...
-    float u_spec;      // ... and t/(tau ln 2)
-    float pad3;
+    float u_spec;      // mixed form: (t + h)/(tau ln 2) of the candidate state
+    float u_scale;     // mixed form: 1/(tau ln 2)
 };
 
 struct PlanDev {
@@ -148,6 +147,7 @@ struct OptsDev {
     float mlp_margin;  // the proposal uses e^(out - margin)
     // FP32 guard band of the mixed form's accept test (see update_reduce)
     float eps_r32, ymin_lo32, ymin_hi32, band_lo32, band_hi32, kappa32;
+    float eps_c32, ga32, gb32, grow32;  // mixed form: eps_c and the growth factor's terms in FP32
     int learn;   // 1: propose with the network
     int record;  // 1: write (features, label) at every accepted state
     int mlp_smem_off;  // byte offset of the staged network in the CTA's shared memory
