@@ -140,18 +140,22 @@ static kn_status build_tables(kn_network* n, int prec, int Q, Tables& T) {
     }
     const int Tn = (int)fidx.size();
     const int C = (Tn + Q - 1) / Q;
-    std::vector<uint32_t> terms((size_t)C * Q);
+    const int fspan = fk_span(N, prec == kPrecFP64 ? 8 : 4);
+    if (fspan + 2 * Q > (int)kTermRowMask) return fail(KN_ERR_INVALID_ARG, "network too large for the gather encoding");
+    // two extra rows of zero terms: the gather loop loads two terms ahead
+    // without a bounds test
+    std::vector<uint32_t> terms((size_t)(C + 2) * Q, (uint32_t)zero_idx);
     for (int c = 0; c < Q; ++c)
         for (int k = 0; k < C; ++k) {
             const int p = c * C + k;
             uint32_t w;
             if (p < Tn) {
                 const int r = frow[p];
-                w = fidx[p] | ((uint32_t)r << kTermRowShift);
-                if (p == rend[r]) {
-                    w |= kTermEnd;
-                    if (rstart[r] < c * C) w |= kTermHead;
-                }
+                // a row's last term in this chunk stores the running sum: to the
+                // row itself, or to chunk c's head partial if the row began earlier
+                const int slot = rstart[r] < c * C ? fspan + c : r;
+                w = fidx[p] | ((uint32_t)slot << kTermRowShift);
+                if (p == rend[r]) w |= kTermEnd;
             } else {
                 w = (uint32_t)zero_idx;
             }
@@ -177,7 +181,7 @@ static kn_status build_tables(kn_network* n, int prec, int Q, Tables& T) {
     tl.off_cexp = off;
     off = pad16(off + real * R);
     tl.off_terms = off;
-    off = pad16(off + 4 * C * Q);
+    off = pad16(off + 4 * (C + 2) * Q);
     tl.off_fix = off;
     off = pad16(off + 2 * (int)fix.size());
     tl.bytes = off;
@@ -246,7 +250,7 @@ static GroupLayout group_layout(const kn_network* n, int prec, int G, bool feat)
     g.off_Fk = off;
     off = pad16(off + real * 2 * n->N);
     g.off_carry = off;
-    off = pad16(off + 8 * 2 * G);
+    off = pad16(off + real * 2 * G);
     g.off_red = off;
     off = pad16(off + (G / 32) * (8 * 3 + 4 + 4));
     g.off_feat = off;
@@ -630,19 +634,27 @@ static kn_status prepare_launch(kn_network* const* nets, int n_nets, const kn_op
             }
         }
         if (!P_best && n_nets == 1 && !o->threads_per_cta) {
-            // one network, no explicit CTA size: the most zone groups per CTA
-            // (tables staged in shared memory), then the smallest group
+            // one network, no explicit CTA size, tables staged in shared memory.
+            // Single-warp groups (small networks): the most groups per CTA,
+            // which hides their short serial sections behind one another.
+            // Larger groups: up to kTargetGroups groups, then the largest group
+            // (shorter gather chunks); measured on the 150-species network,
+            // 5 x 192 beats 6 x 160, 5 x 160 and 3 x 320 threads.
             kn_network* n = nets[0];
             Tiling best;
             const int g0 = o->threads_per_zone ? o->threads_per_zone : base_group(n);
             const int g1 = o->threads_per_zone ? o->threads_per_zone : 512;
+            const bool small = g0 == 32;
+            constexpr int kTargetGroups = 5;
             for (int G = g0; G <= g1; G += 32) {
                 Tables* tb;
                 if ((s = get_tables(n, prec, G, &tb)) != KN_OK) return s;
                 const GroupLayout gl = group_layout(n, prec, G, feat);
                 int M = std::min(kMaxGroups, 1024 / G);
+                if (!small) M = std::min(M, kTargetGroups);
                 while (M > 0 && tb->tl.bytes + M * gl.bytes > budget) --M;
-                if (M > best.M) best = Tiling{G, M, 1, tb->tl.bytes + M * gl.bytes};
+                const bool better = small ? M > best.M : (M > best.M || (M == best.M && M > 0));
+                if (better) best = Tiling{G, M, 1, tb->tl.bytes + M * gl.bytes};
             }
             if (best.M > 0) {
                 P_best = best.G * best.M;

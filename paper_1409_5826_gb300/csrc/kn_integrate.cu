@@ -59,12 +59,7 @@ __device__ __forceinline__ double exp_neg_small(double x, int degree) {
     return fma(x, p, 1.0);
 }
 
-// Gather accumulators: plain FP64, or FP32 with Kahan compensation.
-struct AccD {
-    double s;
-    __device__ __forceinline__ void reset() { s = 0.0; }
-    __device__ __forceinline__ void add(double v) { s += v; }
-};
+// Kahan-compensated FP32 sum (combines the chunk partials of long rows).
 struct AccKahan {
     float s, c;  // sum and (negated) lost low part: value = s - c
     __device__ __forceinline__ void reset() { s = 0.f; c = 0.f; }
@@ -79,11 +74,9 @@ struct AccKahan {
 template <int PREC> struct PrecTraits;
 template <> struct PrecTraits<kPrecFP64> {
     using real = double;
-    using Acc = AccD;
 };
 template <> struct PrecTraits<kPrecMixed> {
     using real = float;
-    using Acc = AccKahan;
 };
 
 // ---------------------------------------------------------------------------
@@ -238,7 +231,9 @@ __device__ __forceinline__ void update_reduce_mixed(const PlanDev& P, const Opts
         const float kdt = __fmul_rn(kk, h32);
         float nh, nl, dh, dl;
         if (kdt >= O.kappa32) {
-            nh = __fdiv_rn(fmaf(h32, fp, yh), __fadd_rn(1.f, kdt));
+            // 1 + k dt >= 2; __fdividef is within 2 ulp below 2^126 and gives
+            // 0 above it (an abundance below 2^-126 of y + dt F+)
+            nh = __fdividef(fmaf(h32, fp, yh), __fadd_rn(1.f, kdt));
             nl = 0.f;
             two_sum(nh, -yh, dh, dl);
             dl = __fsub_rn(dl, yl);
@@ -473,6 +468,39 @@ __device__ float mlp_forward_group(const OptsDev& O, const GroupPtrs& g, const u
     return s + Pb[384];
 }
 
+// Mixed form, one reactant-count class of the sorted reactions: reactions
+// j, j + stride, ... below j_end; returns the first index at or past j_end,
+// where the next class continues.  VAR: k_j(t) = K_j 2^(-c_j u).
+template <bool VAR, int NB>
+__device__ __forceinline__ int flux_class(int j, int j_end, int stride, const ushort4* __restrict__ rspec,
+                                          const float* __restrict__ cexp, const float* __restrict__ Kz,
+                                          const float* __restrict__ Y, float* __restrict__ V, float u) {
+#pragma unroll 2
+    for (; j < j_end; j += stride) {
+        const ushort4 rs = rspec[j];
+        float k = Kz[j];
+        if (VAR) k = __fmul_rn(k, ex2_approx(-__fmul_rn(cexp[j], u)));
+        const float ya = Y[rs.x];
+        if (NB == 1) {
+            V[j] = __fmul_rn(k, ya);
+            V[rs.w] = k;
+        } else if (NB == 2) {
+            const float yb = Y[rs.y];
+            V[j] = __fmul_rn(__fmul_rn(k, ya), yb);
+            V[rs.w] = __fmul_rn(k, yb);
+            V[rs.w + 1] = __fmul_rn(k, ya);
+        } else {
+            const float yb = Y[rs.y], yc = Y[rs.z];
+            const float ka = __fmul_rn(k, ya);
+            V[j] = __fmul_rn(__fmul_rn(ka, yb), yc);
+            V[rs.w] = __fmul_rn(__fmul_rn(k, yb), yc);
+            V[rs.w + 1] = __fmul_rn(ka, yc);
+            V[rs.w + 2] = __fmul_rn(ka, yb);
+        }
+    }
+    return j;
+}
+
 // (a) rates k_j(t), fluxes f_j and reactant-slot partials (Eq. 1) of the state
 // in buffer `buf`, over reactions j0, j0 + stride, ...; reactions are sorted
 // 1-, 2-, 3-body, so no multiply by an absent reactant.  s = t / tau (FP64
@@ -516,29 +544,17 @@ __device__ __forceinline__ void flux_pass(const PlanDev& P, const GroupPtrs& g, 
         }
     } else {
         const float* __restrict__ Yc32 = g.Y32 + buf * NP1;
-        const bool varying = !constant;
-#pragma unroll 2
-        for (int j = j0; j < R; j += stride) {
-            const ushort4 rs = rspec[j];
-            float k = (float)Kz[j];
-            if (varying) k = __fmul_rn(k, ex2_approx(-__fmul_rn((float)cexp[j], u)));
-            const float ya = Yc32[rs.x];
-            if (j < R1) {
-                Vw[j] = (real)__fmul_rn(k, ya);
-                Vw[rs.w] = (real)k;
-            } else if (j < R12) {
-                const float yb = Yc32[rs.y];
-                Vw[j] = (real)__fmul_rn(__fmul_rn(k, ya), yb);
-                Vw[rs.w] = (real)__fmul_rn(k, yb);
-                Vw[rs.w + 1] = (real)__fmul_rn(k, ya);
-            } else {
-                const float yb = Yc32[rs.y], yc = Yc32[rs.z];
-                const float ka = __fmul_rn(k, ya);
-                Vw[j] = (real)__fmul_rn(__fmul_rn(ka, yb), yc);
-                Vw[rs.w] = (real)__fmul_rn(__fmul_rn(k, yb), yc);
-                Vw[rs.w + 1] = (real)__fmul_rn(ka, yc);
-                Vw[rs.w + 2] = (real)__fmul_rn(ka, yb);
-            }
+        const float* __restrict__ cf = (const float*)g.cexp;
+        const float* __restrict__ Kf = (const float*)g.K;
+        float* __restrict__ Vf = (float*)g.V;
+        if (constant) {
+            int j = flux_class<false, 1>(j0, R1, stride, rspec, cf, Kf, Yc32, Vf, u);
+            j = flux_class<false, 2>(j, R12, stride, rspec, cf, Kf, Yc32, Vf, u);
+            flux_class<false, 3>(j, R, stride, rspec, cf, Kf, Yc32, Vf, u);
+        } else {
+            int j = flux_class<true, 1>(j0, R1, stride, rspec, cf, Kf, Yc32, Vf, u);
+            j = flux_class<true, 2>(j, R12, stride, rspec, cf, Kf, Yc32, Vf, u);
+            flux_class<true, 3>(j, R, stride, rspec, cf, Kf, Yc32, Vf, u);
         }
     }
 }
@@ -698,54 +714,31 @@ __device__ void run_group(const PlanDev& P, const OptsDev& O, const unsigned cha
                     const uint32_t* __restrict__ tp = terms + lane;
                     const real* __restrict__ Vr = V;
                     real* __restrict__ Fw = Fk;
-                    const uint32_t zterm = (uint32_t)P.zero_idx;
                     uint32_t w0 = tp[0];
-                    uint32_t w1 = C > 1 ? tp[Q] : zterm;
+                    uint32_t w1 = tp[Q];  // rows C and C + 1 of the list are zero terms
                     real v0 = Vr[w0 & 0xffffu];
                     real v1 = Vr[w1 & 0xffffu];
-                    if (PREC == kPrecFP64) {
-                        double* __restrict__ carry = (double*)(gbase + P.gl.off_carry);
-                        double acc = 0.0;
-                        for (int k = 0; k < C; ++k) {
-                            const uint32_t w2 = k + 2 < C ? tp[(k + 2) * Q] : zterm;
-                            const real v2 = Vr[w2 & 0xffffu];
-                            acc += (double)v0;
-                            if (w0 & kTermEnd) {
-                                if (w0 & kTermHead)
-                                    carry[lane] = acc;
-                                else
-                                    Fw[(w0 >> kTermRowShift) & kTermRowMask] = (real)acc;
-                                acc = 0.0;
-                            }
-                            w0 = w1;
-                            v0 = v1;
-                            w1 = w2;
-                            v1 = v2;
+                    // FP64 form: FP64 sums.  Mixed form: plain FP32 sums; every
+                    // term of a row is positive, so a chunk's partial of at most
+                    // C terms is within (C - 1) 2^-24 of its value, relative,
+                    // and the partials of rows that cross chunks are combined
+                    // compensated below.
+                    real acc = (real)0;
+#pragma unroll 4
+                    for (int k = 0; k < C; ++k) {
+                        const uint32_t w2 = tp[(k + 2) * Q];
+                        const real v2 = Vr[w2 & 0xffffu];
+                        acc = acc + v0;
+                        if ((int)w0 < 0) {  // END
+                            Fw[(w0 >> kTermRowShift) & kTermRowMask] = acc;
+                            acc = (real)0;
                         }
-                        carry[Q + lane] = acc;
-                    } else {
-                        // FP32 Kahan sums; no FP64 instruction in this loop
-                        float2* __restrict__ carry = (float2*)(gbase + P.gl.off_carry);
-                        AccKahan ak;
-                        ak.reset();
-                        for (int k = 0; k < C; ++k) {
-                            const uint32_t w2 = k + 2 < C ? tp[(k + 2) * Q] : zterm;
-                            const real v2 = Vr[w2 & 0xffffu];
-                            ak.add((float)v0);
-                            if (w0 & kTermEnd) {
-                                if (w0 & kTermHead)
-                                    carry[lane] = make_float2(ak.s, ak.c);
-                                else
-                                    Fw[(w0 >> kTermRowShift) & kTermRowMask] = (real)__fsub_rn(ak.s, ak.c);
-                                ak.reset();
-                            }
-                            w0 = w1;
-                            v0 = v1;
-                            w1 = w2;
-                            v1 = v2;
-                        }
-                        carry[Q + lane] = make_float2(ak.s, ak.c);
+                        w0 = w1;
+                        v0 = v1;
+                        w1 = w2;
+                        v1 = v2;
                     }
+                    ((real*)(gbase + P.gl.off_carry))[Q + lane] = acc;  // the open partial
                 }
                 gs.sync();
                 // (c) rows that cross chunk boundaries: tails of c0..c1-1, head of c1
@@ -758,15 +751,11 @@ __device__ void run_group(const PlanDev& P, const OptsDev& O, const unsigned cha
                         s += carry[fx.z];
                         Fk[fx.x] = (real)s;
                     } else {
-                        const float2* carry = (const float2*)(gbase + P.gl.off_carry);
+                        const float* carry = (const float*)(gbase + P.gl.off_carry);
                         AccKahan ak;
                         ak.reset();
-                        for (int c = fx.y; c < fx.z; ++c) {
-                            ak.add(carry[Q + c].x);
-                            ak.add(-carry[Q + c].y);
-                        }
-                        ak.add(carry[fx.z].x);
-                        ak.add(-carry[fx.z].y);
+                        for (int c = fx.y; c < fx.z; ++c) ak.add(carry[Q + c]);
+                        ak.add(carry[fx.z]);
                         Fk[fx.x] = (real)__fsub_rn(ak.s, ak.c);
                     }
                 }

@@ -10,13 +10,20 @@ namespace kn {
 // Term encoding of the flat gather list (one 32-bit word per term):
 //   bits  0..15  index into the zone's value array V (a flux f_j, a reactant-
 //                slot partial, or the constant-zero entry)
-//   bits 16..26  output row: 0..N-1 are F+_i, N..2N-1 are k_i
-//   bit  27      END: the row's last term inside this chunk
-//   bit  28      HEAD: the row began in an earlier chunk (write to the carry)
+//   bits 16..30  output slot of the row sum, an index into the zone's Fk array
+//                extended by the chunk partials: 0..N-1 are F+_i, N..2N-1 are
+//                k_i; a row that began in an earlier chunk c' < c ends in chunk
+//                c at slot fk_span + c (the head partial of chunk c), and the
+//                partial left open at the end of chunk c goes to fk_span + Q + c
+//   bit  31      END: the row's last term inside this chunk (the sign bit, so
+//                the test is one compare and the store a predicated one)
 constexpr uint32_t kTermRowShift = 16;
-constexpr uint32_t kTermRowMask = 0x7ffu;
-constexpr uint32_t kTermEnd = 1u << 27;
-constexpr uint32_t kTermHead = 1u << 28;
+constexpr uint32_t kTermRowMask = 0x7fffu;
+constexpr uint32_t kTermEnd = 1u << 31;
+
+// Fk holds 2N values of `real_bytes` each, padded to 16 bytes; the chunk
+// partials follow directly, so slot fk_span + c addresses them through Fk.
+constexpr int fk_span(int N, int real_bytes) { return ((real_bytes * 2 * N + 15) & ~15) / real_bytes; }
 
 constexpr int kMaxSpecies = 1023;
 constexpr int kMaxPlans = 4;      // networks per launch
@@ -54,7 +61,7 @@ struct GroupLayout {
                         //   the low parts of the float-float abundances (0 at entry N)
     int32_t off_Y32;    // float[2][N + 1] (mixed only): the high parts, entry N the constant 1
     int32_t off_Fk;     // real[2N]: F+ then k (mixed: Kahan sums rounded to float)
-    int32_t off_carry;  // FP64: double[2][Q]; mixed: float2[2][Q] Kahan (sum, compensation)
+    int32_t off_carry;  // chunk partials of rows that cross chunks: real[2][Q] (head, tail)
     int32_t off_red;    // per-warp reduction scratch, W = G/32 warps: double[W] x 3, float[W], int[W]
     int32_t off_feat;   // learned proposal / records: float[64 feats, 64 inputs, 128 h1, 128 h2],
                         //   int[3][64] histograms + 4 counters (absent when unused)
