@@ -139,27 +139,26 @@ static kn_status build_tables(kn_network* n, int prec, int Q, Tables& T) {
         rend[r] = (int)fidx.size() - 1;
     }
     const int Tn = (int)fidx.size();
-    const int C = (Tn + Q - 1) / Q;
-    const int fspan = fk_span(N, prec == kPrecFP64 ? 8 : 4);
-    if (fspan + 2 * Q > (int)kTermRowMask) return fail(KN_ERR_INVALID_ARG, "network too large for the gather encoding");
-    // two extra rows of zero terms: the gather loop loads two terms ahead
-    // without a bounds test
-    std::vector<uint32_t> terms((size_t)(C + 2) * Q, (uint32_t)zero_idx);
-    for (int c = 0; c < Q; ++c)
+    // C terms per chunk (even: the loop takes pairs), Qa <= Q chunks
+    int C = (Tn + Q - 1) / Q;
+    C += C & 1;
+    const int Qa = (Tn + C - 1) / C;
+    const int real_bytes = prec == kPrecFP64 ? 8 : 4;
+    const int fspan = fk_span(N, real_bytes);
+    if ((fspan + 2 * Qa) * real_bytes > 0xffff)
+        return fail(KN_ERR_INVALID_ARG, "network too large for the gather encoding");
+    std::vector<uint32_t> terms((size_t)(C + 2) * Qa, (uint32_t)zero_idx);
+    for (int c = 0; c < Qa; ++c)
         for (int k = 0; k < C; ++k) {
             const int p = c * C + k;
-            uint32_t w;
-            if (p < Tn) {
-                const int r = frow[p];
-                // a row's last term in this chunk stores the running sum: to the
-                // row itself, or to chunk c's head partial if the row began earlier
-                const int slot = rstart[r] < c * C ? fspan + c : r;
-                w = fidx[p] | ((uint32_t)slot << kTermRowShift);
-                if (p == rend[r]) w |= kTermEnd;
-            } else {
-                w = (uint32_t)zero_idx;
-            }
-            terms[(size_t)k * Q + c] = w;
+            if (p >= Tn) continue;  // zero term
+            const int r = frow[p];
+            // a row's last term in this chunk stores the running sum: to the
+            // row itself, or to chunk c's head partial if the row began earlier
+            const int slot = rstart[r] < c * C ? fspan + c : r;
+            uint32_t w = fidx[p] | ((uint32_t)(slot * real_bytes) << kTermDstShift);
+            if (p == rend[r]) w |= kTermEnd;
+            terms[((size_t)(k >> 1) * Qa + c) * 2 + (k & 1)] = w;
         }
     std::vector<uint16_t> fix;
     for (int r = 0; r < 2 * N; ++r) {
@@ -181,7 +180,7 @@ static kn_status build_tables(kn_network* n, int prec, int Q, Tables& T) {
     tl.off_cexp = off;
     off = pad16(off + real * R);
     tl.off_terms = off;
-    off = pad16(off + 4 * (C + 2) * Q);
+    off = pad16(off + 4 * (C + 2) * Qa);
     tl.off_fix = off;
     off = pad16(off + 2 * (int)fix.size());
     tl.bytes = off;
@@ -217,7 +216,7 @@ static kn_status build_tables(kn_network* n, int prec, int Q, Tables& T) {
     KN_CUDA(cudaMemcpy(T.blob->p, blob.data(), off, cudaMemcpyHostToDevice));
     T.tl = tl;
     T.C = C;
-    T.Q = Q;
+    T.Q = Qa;
     T.n_fix = (int)fix.size() / 4;
     return KN_OK;
 }
@@ -437,7 +436,8 @@ kn_status kn_create_network(const kn_network_desc* d, kn_network** out) {
     }
     KN_CUDA(n->rate0.ensure(16 * (size_t)R));
     KN_CUDA(cudaMemcpy(n->rate0.p, r0.data(), 16 * (size_t)R, cudaMemcpyHostToDevice));
-    if (R + slots + 1 > 65535) return fail(KN_ERR_INVALID_ARG, "network too large for 16-bit gather indices");
+    if (R + slots + 1 > (int)kTermIdxMask)
+        return fail(KN_ERR_INVALID_ARG, "network too large for 15-bit gather indices");
     n->nbar = nsum / R;
     n->rbar = rsum / R;
     KN_CUDA(n->qhead.ensure(64));

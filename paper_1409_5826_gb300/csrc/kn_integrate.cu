@@ -711,32 +711,35 @@ __device__ void run_group(const PlanDev& P, const OptsDev& O, const unsigned cha
                 // (b) balanced gathers: chunk `lane` of the flat term list; the
                 //     next two terms are loaded ahead of the current one's store
                 if (lane < Q) {
-                    const uint32_t* __restrict__ tp = terms + lane;
+                    const uint2* __restrict__ tp = (const uint2*)terms + lane;
                     const real* __restrict__ Vr = V;
-                    real* __restrict__ Fw = Fk;
-                    uint32_t w0 = tp[0];
-                    uint32_t w1 = tp[Q];  // rows C and C + 1 of the list are zero terms
-                    real v0 = Vr[w0 & 0xffffu];
-                    real v1 = Vr[w1 & 0xffffu];
+                    unsigned char* __restrict__ Fb = (unsigned char*)Fk;
                     // FP64 form: FP64 sums.  Mixed form: plain FP32 sums; every
                     // term of a row is positive, so a chunk's partial of at most
                     // C terms is within (C - 1) 2^-24 of its value, relative,
                     // and the partials of rows that cross chunks are combined
                     // compensated below.
+                    uint2 w = tp[0];
+                    real va = Vr[w.x & kTermIdxMask], vb = Vr[w.y & kTermIdxMask];
                     real acc = (real)0;
-#pragma unroll 4
-                    for (int k = 0; k < C; ++k) {
-                        const uint32_t w2 = tp[(k + 2) * Q];
-                        const real v2 = Vr[w2 & 0xffffu];
-                        acc = acc + v0;
-                        if ((int)w0 < 0) {  // END
-                            Fw[(w0 >> kTermRowShift) & kTermRowMask] = acc;
+                    const int C2 = C >> 1;
+#pragma unroll 2
+                    for (int p = 0; p < C2; ++p) {
+                        const uint2 wn = tp[(p + 1) * Q];  // the last row of pairs is zero terms
+                        const real na = Vr[wn.x & kTermIdxMask], nb = Vr[wn.y & kTermIdxMask];
+                        acc = acc + va;
+                        if (w.x & kTermEnd) {
+                            *(real*)(Fb + (w.x >> kTermDstShift)) = acc;
                             acc = (real)0;
                         }
-                        w0 = w1;
-                        v0 = v1;
-                        w1 = w2;
-                        v1 = v2;
+                        acc = acc + vb;
+                        if (w.y & kTermEnd) {
+                            *(real*)(Fb + (w.y >> kTermDstShift)) = acc;
+                            acc = (real)0;
+                        }
+                        w = wn;
+                        va = na;
+                        vb = nb;
                     }
                     ((real*)(gbase + P.gl.off_carry))[Q + lane] = acc;  // the open partial
                 }

@@ -8,18 +8,21 @@
 namespace kn {
 
 // Term encoding of the flat gather list (one 32-bit word per term):
-//   bits  0..15  index into the zone's value array V (a flux f_j, a reactant-
+//   bits  0..14  index into the zone's value array V (a flux f_j, a reactant-
 //                slot partial, or the constant-zero entry)
-//   bits 16..30  output slot of the row sum, an index into the zone's Fk array
-//                extended by the chunk partials: 0..N-1 are F+_i, N..2N-1 are
-//                k_i; a row that began in an earlier chunk c' < c ends in chunk
-//                c at slot fk_span + c (the head partial of chunk c), and the
-//                partial left open at the end of chunk c goes to fk_span + Q + c
-//   bit  31      END: the row's last term inside this chunk (the sign bit, so
-//                the test is one compare and the store a predicated one)
-constexpr uint32_t kTermRowShift = 16;
-constexpr uint32_t kTermRowMask = 0x7fffu;
-constexpr uint32_t kTermEnd = 1u << 31;
+//   bit  15      END: the row's last term inside this chunk
+//   bits 16..31  byte offset, from the zone's Fk array, of the slot that an
+//                END term stores the row's running sum to: slots 0..N-1 are
+//                F+_i, N..2N-1 are k_i; a row that began in an earlier chunk
+//                ends in chunk c at slot fk_span + c (the head partial of chunk
+//                c), and the partial left open at the end of chunk c goes to
+//                slot fk_span + Q + c
+// Terms are stored in pairs, chunk-major: terms 2p and 2p + 1 of chunk c are
+// the two words of uint2 number p Q + c, so a warp's pair loads are
+// contiguous; C is even and one extra row of zero-term pairs follows.
+constexpr uint32_t kTermIdxMask = 0x7fffu;
+constexpr uint32_t kTermEnd = 0x8000u;
+constexpr uint32_t kTermDstShift = 16;
 
 // Fk holds 2N values of `real_bytes` each, padded to 16 bytes; the chunk
 // partials follow directly, so slot fk_span + c addresses them through Fk.
