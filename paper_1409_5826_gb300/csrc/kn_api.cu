@@ -75,7 +75,8 @@ struct DevBuf {
 struct Tables {
     std::unique_ptr<DevBuf> blob;
     TableLayout tl{};
-    int C = 0, Q = 0, n_fix = 0;
+    int n_fix = 0;
+    int L = 0, n_slices = 0, warp_len = 0;  // piece cap, slices, longest warp's terms per lane
 };
 }  // namespace kn
 
@@ -127,49 +128,105 @@ static kn_status build_tables(kn_network* n, int prec, int Q, Tables& T) {
         }
         for (int q = 0; q < n->nr[j]; ++q) rows[N + n->reac[j * 3 + q]].push_back((uint16_t)(R + sslot0[jn] + q));
     }
-    std::vector<uint16_t> fidx;
-    std::vector<int> frow, rstart(2 * N), rend(2 * N);
-    for (int r = 0; r < 2 * N; ++r) {
+    for (int r = 0; r < 2 * N; ++r)
         if (rows[r].empty()) rows[r].push_back((uint16_t)zero_idx);  // row written as 0
-        rstart[r] = (int)fidx.size();
-        for (uint16_t v : rows[r]) {
-            fidx.push_back(v);
-            frow.push_back(r);
-        }
-        rend[r] = (int)fidx.size() - 1;
-    }
-    const int Tn = (int)fidx.size();
-    // C terms per chunk (even: the loop takes pairs), Qa <= Q chunks
-    int C = (Tn + Q - 1) / Q;
-    C += C & 1;
-    const int Qa = (Tn + C - 1) / C;
     const int real_bytes = prec == kPrecFP64 ? 8 : 4;
     const int fspan = fk_span(N, real_bytes);
-    if ((fspan + 2 * Qa) * real_bytes > 0xffff)
-        return fail(KN_ERR_INVALID_ARG, "network too large for the gather encoding");
-    std::vector<uint32_t> terms((size_t)(C + 2) * Qa, (uint32_t)zero_idx);
-    for (int c = 0; c < Qa; ++c)
-        for (int k = 0; k < C; ++k) {
-            const int p = c * C + k;
-            if (p >= Tn) continue;  // zero term
-            const int r = frow[p];
-            // a row's last term in this chunk stores the running sum: to the
-            // row itself, or to chunk c's head partial if the row began earlier
-            const int slot = rstart[r] < c * C ? fspan + c : r;
-            uint32_t w = fidx[p] | ((uint32_t)(slot * real_bytes) << kTermDstShift);
-            if (p == rend[r]) w |= kTermEnd;
-            terms[((size_t)(k >> 1) * Qa + c) * 2 + (k & 1)] = w;
+    const int G = Q, W = G / 32;
+    const int spare = fspan + 2 * G - 1;
+    if ((spare + 1) * real_bytes > 0xffff) return fail(KN_ERR_INVALID_ARG, "network too large for the gather tables");
+    size_t maxlen = 0;
+    for (auto& r : rows) maxlen = std::max(maxlen, r.size());
+    // One layout for a piece cap L: pieces, slices, and the slices' warps
+    // (longest-first onto the least-loaded warp).  Its cost is the longest
+    // warp's terms per lane plus the longest fix-up.
+    struct Piece {
+        int row, start, len, dst;
+    };
+    struct Layout {
+        std::vector<Piece> pieces;
+        std::vector<uint16_t> fix;
+        std::vector<std::vector<int>> warp_slices;  // slice ids per warp
+        std::vector<int> slice_len;
+        int cost = 1 << 30, warp_len = 0;
+    };
+    auto layout_for = [&](int L, Layout& out) -> bool {
+        Layout lo;
+        int n_part = 0, max_fix = 0;
+        for (int r = 0; r < 2 * N; ++r) {
+            const int len = (int)rows[r].size();
+            if (len <= L) {
+                lo.pieces.push_back({r, 0, len, r * real_bytes});
+                continue;
+            }
+            const int np = (len + L - 1) / L;
+            lo.fix.push_back((uint16_t)(r * real_bytes));
+            lo.fix.push_back((uint16_t)n_part);
+            lo.fix.push_back((uint16_t)np);
+            lo.fix.push_back(0);
+            for (int q = 0, st = 0; q < np; ++q) {
+                const int pl = len / np + (q < len % np ? 1 : 0);
+                lo.pieces.push_back({r, st, pl, (fspan + n_part) * real_bytes});
+                st += pl;
+                ++n_part;
+            }
+            max_fix = std::max(max_fix, np);
         }
-    std::vector<uint16_t> fix;
-    for (int r = 0; r < 2 * N; ++r) {
-        const int c0 = rstart[r] / C, c1 = rend[r] / C;
-        if (c0 != c1) {
-            fix.push_back((uint16_t)r);
-            fix.push_back((uint16_t)c0);
-            fix.push_back((uint16_t)c1);
-            fix.push_back(0);
+        if (n_part > 2 * G - 1) return false;  // partials and the spare share the 2G carry slots
+        std::stable_sort(lo.pieces.begin(), lo.pieces.end(),
+                         [](const Piece& x, const Piece& y) { return x.len > y.len; });
+        while (lo.pieces.size() % 32) lo.pieces.push_back({-1, 0, 0, spare * real_bytes});
+        const int ns = (int)lo.pieces.size() / 32;
+        for (int s = 0; s < ns; ++s) lo.slice_len.push_back(lo.pieces[32 * s].len);
+        std::vector<int> order(ns);
+        for (int s = 0; s < ns; ++s) order[s] = s;
+        std::stable_sort(order.begin(), order.end(),
+                         [&](int x, int y) { return lo.slice_len[x] > lo.slice_len[y]; });
+        lo.warp_slices.assign(W, {});
+        std::vector<int> load(W, 0);
+        for (int s : order) {
+            const int w = (int)(std::min_element(load.begin(), load.end()) - load.begin());
+            lo.warp_slices[w].push_back(s);
+            load[w] += lo.slice_len[s];
+        }
+        lo.warp_len = *std::max_element(load.begin(), load.end());
+        lo.cost = lo.warp_len + 2 * max_fix;
+        out = std::move(lo);
+        return true;
+    };
+    Layout best;
+    int L_best = 0;
+    for (int L = 1; L <= (int)maxlen; ++L) {
+        Layout lo;
+        if (!layout_for(L, lo)) continue;
+        if (lo.cost < best.cost || (lo.cost == best.cost && lo.fix.size() <= best.fix.size())) {
+            best = std::move(lo);
+            L_best = L;
         }
     }
+    if (!L_best) return fail(KN_ERR_INVALID_ARG, "no gather layout fits %d threads per zone", G);
+    // flatten: slices in warp order
+    std::vector<uint16_t> wsl(W + 1, 0), sdst, sidx;
+    std::vector<uint32_t> shdr;
+    int n_slices = 0;
+    for (int w = 0; w < W; ++w) {
+        wsl[w] = (uint16_t)n_slices;
+        for (int s : best.warp_slices[w]) {
+            const int len = best.slice_len[s];
+            shdr.push_back((uint32_t)sidx.size());
+            shdr.push_back((uint32_t)len);
+            const size_t base = sidx.size();
+            sidx.resize(base + 32 * (size_t)len, (uint16_t)zero_idx);
+            for (int l = 0; l < 32; ++l) {
+                const Piece& pc = best.pieces[32 * s + l];
+                sdst.push_back((uint16_t)pc.dst);
+                for (int k = 0; k < pc.len; ++k) sidx[base + 32 * (size_t)k + l] = rows[pc.row][pc.start + k];
+            }
+            ++n_slices;
+        }
+    }
+    wsl[W] = (uint16_t)n_slices;
+    const std::vector<uint16_t>& fix = best.fix;
     const int real = prec == kPrecFP64 ? 8 : 4;
     TableLayout tl{};
     int off = 0;
@@ -179,8 +236,14 @@ static kn_status build_tables(kn_network* n, int prec, int Q, Tables& T) {
     off = pad16(off + 8 * R);
     tl.off_cexp = off;
     off = pad16(off + real * R);
-    tl.off_terms = off;
-    off = pad16(off + 4 * (C + 2) * Qa);
+    tl.off_wsl = off;
+    off = pad16(off + 2 * (W + 1));
+    tl.off_shdr = off;
+    off = pad16(off + 4 * (int)shdr.size());
+    tl.off_sdst = off;
+    off = pad16(off + 2 * (int)sdst.size());
+    tl.off_sidx = off;
+    off = pad16(off + 2 * (int)sidx.size());
     tl.off_fix = off;
     off = pad16(off + 2 * (int)fix.size());
     tl.bytes = off;
@@ -209,15 +272,19 @@ static kn_status build_tables(kn_network* n, int prec, int Q, Tables& T) {
             memcpy(blob.data() + tl.off_cexp + 4 * jn, &cf, 4);
         }
     }
-    memcpy(blob.data() + tl.off_terms, terms.data(), 4 * terms.size());
+    memcpy(blob.data() + tl.off_wsl, wsl.data(), 2 * wsl.size());
+    memcpy(blob.data() + tl.off_shdr, shdr.data(), 4 * shdr.size());
+    memcpy(blob.data() + tl.off_sdst, sdst.data(), 2 * sdst.size());
+    memcpy(blob.data() + tl.off_sidx, sidx.data(), 2 * sidx.size());
     if (!fix.empty()) memcpy(blob.data() + tl.off_fix, fix.data(), 2 * fix.size());
     T.blob.reset(new DevBuf());
     KN_CUDA(T.blob->ensure(off));
     KN_CUDA(cudaMemcpy(T.blob->p, blob.data(), off, cudaMemcpyHostToDevice));
     T.tl = tl;
-    T.C = C;
-    T.Q = Qa;
     T.n_fix = (int)fix.size() / 4;
+    T.L = L_best;
+    T.n_slices = n_slices;
+    T.warp_len = best.warp_len;
     return KN_OK;
 }
 
@@ -436,8 +503,7 @@ kn_status kn_create_network(const kn_network_desc* d, kn_network** out) {
     }
     KN_CUDA(n->rate0.ensure(16 * (size_t)R));
     KN_CUDA(cudaMemcpy(n->rate0.p, r0.data(), 16 * (size_t)R, cudaMemcpyHostToDevice));
-    if (R + slots + 1 > (int)kTermIdxMask)
-        return fail(KN_ERR_INVALID_ARG, "network too large for 15-bit gather indices");
+    if (R + slots + 1 > 0xffff) return fail(KN_ERR_INVALID_ARG, "network too large for 16-bit gather indices");
     n->nbar = nsum / R;
     n->rbar = rsum / R;
     KN_CUDA(n->qhead.ensure(64));
@@ -701,8 +767,6 @@ static kn_status prepare_launch(kn_network* const* nets, int n_nets, const kn_op
         P.N = n->N;
         P.R = n->R;
         P.S_r = n->S_r;
-        P.C = tb->C;
-        P.Q = tb->Q;
         P.n_fix = tb->n_fix;
         P.zero_idx = n->R + n->S_r;
         P.smem_tables = t.smem_tables;
@@ -976,8 +1040,6 @@ kn_status noalloc_prepare(kn_network* n, const kn_opts* o, int32_t n_zones, cons
     Pd.N = n->N;
     Pd.R = n->R;
     Pd.S_r = n->S_r;
-    Pd.C = tb.C;
-    Pd.Q = tb.Q;
     Pd.n_fix = tb.n_fix;
     Pd.zero_idx = n->R + n->S_r;
     Pd.smem_tables = smem_tables;

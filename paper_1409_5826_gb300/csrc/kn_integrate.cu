@@ -12,9 +12,9 @@
 //     list) are staged once per CTA into shared memory and shared by all
 //     groups;
 //   * per step: rates + fluxes + reactant-slot partials (one pass over
-//     reactions), balanced chunked gathers of F+ and k (every thread sums the
-//     same number of terms; rows cut by a chunk boundary are fixed up from
-//     per-chunk carries), then the kappa-switched FP64 update with
+//     reactions), sliced gathers of F+ and k (each lane sums one row piece
+//     per slice with no per-term branch; long rows are split and their
+//     partials summed afterwards), then the kappa-switched update with
 //     deterministic group reductions for the accept test.
 //   * no spin-waits: every loop is bounded by the zone's step and reject limits.
 #include <cuda_bf16.h>
@@ -128,7 +128,10 @@ struct GroupPtrs {
     const void* A;  // real[N]
     const ushort4* rspec;
     const void* cexp;
-    const uint32_t* terms;
+    const uint16_t* wsl;
+    const uint2* shdr;
+    const uint16_t* sdst;
+    const uint16_t* sidx;
     const ushort4* fix;
     unsigned char* gbase;
     void* V;
@@ -563,7 +566,7 @@ template <int PREC, bool FEAT>
 __device__ void run_group(const PlanDev& P, const OptsDev& O, const unsigned char* tb, const unsigned char* mlp_smem,
                           unsigned char* gbase, const int lane, const GroupSync gs) {
     using real = typename PrecTraits<PREC>::real;
-    const int N = P.N, R = P.R, G = P.G, Q = P.Q, C = P.C, NP1 = N + 1;
+    const int N = P.N, R = P.R, G = P.G, NP1 = N + 1;
     const int R1 = P.R1, R12 = P.R12;
     const bool feats_on = FEAT && (O.learn || O.record);
 
@@ -571,7 +574,10 @@ __device__ void run_group(const PlanDev& P, const OptsDev& O, const unsigned cha
     g.A = tb + P.tl.off_A;
     g.rspec = (const ushort4*)(tb + P.tl.off_rspec);
     g.cexp = tb + P.tl.off_cexp;
-    g.terms = (const uint32_t*)(tb + P.tl.off_terms);
+    g.wsl = (const uint16_t*)(tb + P.tl.off_wsl);
+    g.shdr = (const uint2*)(tb + P.tl.off_shdr);
+    g.sdst = (const uint16_t*)(tb + P.tl.off_sdst);
+    g.sidx = (const uint16_t*)(tb + P.tl.off_sidx);
     g.fix = (const ushort4*)(tb + P.tl.off_fix);
     g.gbase = gbase;
     g.V = gbase + P.gl.off_V;
@@ -591,7 +597,6 @@ __device__ void run_group(const PlanDev& P, const OptsDev& O, const unsigned cha
     g.feat = (float*)(gbase + P.gl.off_feat);
     g.hist = (int*)(g.feat + 384);
 
-    const uint32_t* __restrict__ terms = g.terms;
     const ushort4* __restrict__ fix = g.fix;
     real* V = (real*)g.V;
     real* K = (real*)g.K;
@@ -708,61 +713,47 @@ __device__ void run_group(const PlanDev& P, const OptsDev& O, const unsigned cha
                     flux_pass<PREC>(P, g, lane, G, cur, S.constant, S.s, S.u, S.poly);
                     gs.sync();
                 }
-                // (b) balanced gathers: chunk `lane` of the flat term list; the
-                //     next two terms are loaded ahead of the current one's store
-                if (lane < Q) {
-                    const uint2* __restrict__ tp = (const uint2*)terms + lane;
-                    const real* __restrict__ Vr = V;
+                // (b) sliced gathers: warp w sums its slices, one row piece per
+                //     lane, and stores each piece's sum (FP64 form: FP64 sums;
+                //     mixed form: plain FP32 sums -- every term of a row is
+                //     positive, so a piece of at most L terms is within
+                //     (L - 1) 2^-24 of its value, relative)
+                {
+                    const int w = lane >> 5, l = lane & 31;
+                    const int s1 = g.wsl[w + 1];
                     unsigned char* __restrict__ Fb = (unsigned char*)Fk;
-                    // FP64 form: FP64 sums.  Mixed form: plain FP32 sums; every
-                    // term of a row is positive, so a chunk's partial of at most
-                    // C terms is within (C - 1) 2^-24 of its value, relative,
-                    // and the partials of rows that cross chunks are combined
-                    // compensated below.
-                    uint2 w = tp[0];
-                    real va = Vr[w.x & kTermIdxMask], vb = Vr[w.y & kTermIdxMask];
-                    real acc = (real)0;
-                    const int C2 = C >> 1;
-#pragma unroll 2
-                    for (int p = 0; p < C2; ++p) {
-                        const uint2 wn = tp[(p + 1) * Q];  // the last row of pairs is zero terms
-                        const real na = Vr[wn.x & kTermIdxMask], nb = Vr[wn.y & kTermIdxMask];
-                        acc = acc + va;
-                        if (w.x & kTermEnd) {
-                            *(real*)(Fb + (w.x >> kTermDstShift)) = acc;
-                            acc = (real)0;
-                        }
-                        acc = acc + vb;
-                        if (w.y & kTermEnd) {
-                            *(real*)(Fb + (w.y >> kTermDstShift)) = acc;
-                            acc = (real)0;
-                        }
-                        w = wn;
-                        va = na;
-                        vb = nb;
-                    }
-                    ((real*)(gbase + P.gl.off_carry))[Q + lane] = acc;  // the open partial
-                }
-                gs.sync();
-                // (c) rows that cross chunk boundaries: tails of c0..c1-1, head of c1
-                for (int f = lane; f < P.n_fix; f += G) {
-                    const ushort4 fx = fix[f];
-                    if (PREC == kPrecFP64) {
-                        const double* carry = (const double*)(gbase + P.gl.off_carry);
-                        double s = 0.0;
-                        for (int c = fx.y; c < fx.z; ++c) s += carry[Q + c];
-                        s += carry[fx.z];
-                        Fk[fx.x] = (real)s;
-                    } else {
-                        const float* carry = (const float*)(gbase + P.gl.off_carry);
-                        AccKahan ak;
-                        ak.reset();
-                        for (int c = fx.y; c < fx.z; ++c) ak.add(carry[Q + c]);
-                        ak.add(carry[fx.z]);
-                        Fk[fx.x] = (real)__fsub_rn(ak.s, ak.c);
+                    const real* __restrict__ Vr = V;
+                    for (int sl = g.wsl[w]; sl < s1; ++sl) {
+                        const uint2 hd = g.shdr[sl];
+                        const uint16_t* __restrict__ ix = g.sidx + hd.x + l;
+                        const int len = (int)hd.y;
+                        real acc = (real)0;
+#pragma unroll 4
+                        for (int k = 0; k < len; ++k) acc = acc + Vr[ix[32 * k]];
+                        *(real*)(Fb + g.sdst[32 * sl + l]) = acc;
                     }
                 }
                 gs.sync();
+                // (c) rows split into pieces: the sum of their partials
+                //     (compensated in the mixed form)
+                if (P.n_fix) {
+                    const real* part = (const real*)(gbase + P.gl.off_carry);
+                    unsigned char* __restrict__ Fb = (unsigned char*)Fk;
+                    for (int f = lane; f < P.n_fix; f += G) {
+                        const ushort4 fx = fix[f];
+                        if (PREC == kPrecFP64) {
+                            double sum = 0.0;
+                            for (int p = fx.y; p < fx.y + fx.z; ++p) sum += (double)part[p];
+                            *(real*)(Fb + fx.x) = (real)sum;
+                        } else {
+                            AccKahan ak;
+                            ak.reset();
+                            for (int p = fx.y; p < fx.y + fx.z; ++p) ak.add((float)part[p]);
+                            *(real*)(Fb + fx.x) = (real)__fsub_rn(ak.s, ak.c);
+                        }
+                    }
+                    gs.sync();
+                }
             }
 
             // features of a state reached by an accepted step: training records

@@ -7,22 +7,18 @@
 
 namespace kn {
 
-// Term encoding of the flat gather list (one 32-bit word per term):
-//   bits  0..14  index into the zone's value array V (a flux f_j, a reactant-
-//                slot partial, or the constant-zero entry)
-//   bit  15      END: the row's last term inside this chunk
-//   bits 16..31  byte offset, from the zone's Fk array, of the slot that an
-//                END term stores the row's running sum to: slots 0..N-1 are
-//                F+_i, N..2N-1 are k_i; a row that began in an earlier chunk
-//                ends in chunk c at slot fk_span + c (the head partial of chunk
-//                c), and the partial left open at the end of chunk c goes to
-//                slot fk_span + Q + c
-// Terms are stored in pairs, chunk-major: terms 2p and 2p + 1 of chunk c are
-// the two words of uint2 number p Q + c, so a warp's pair loads are
-// contiguous; C is even and one extra row of zero-term pairs follows.
-constexpr uint32_t kTermIdxMask = 0x7fffu;
-constexpr uint32_t kTermEnd = 0x8000u;
-constexpr uint32_t kTermDstShift = 16;
+// Sliced gather list (the SELL-C-sigma layout of Kreutzer et al., SIAM J.
+// Sci. Comput. 36 (2014), with slices of C = 32 rows, one per warp lane).
+// The 2N row sums -- F+_i (rows 0..N-1: a flux f_j per product slot naming
+// i) and k_i (rows N..2N-1: a reactant-slot partial per slot naming i) --
+// are cut into pieces of at most L terms, sorted by length and packed 32 to
+// a slice.  Slice s has length len_s (its longest piece) and holds lane l's
+// term k at sidx[base_s + 32 k + l] (a V index; shorter pieces are padded
+// with the constant-zero entry).  Warp w of a zone group sums slices
+// wsl[w] .. wsl[w + 1] - 1 and stores lane l's sum at byte offset
+// sdst[32 s + l] from the zone's Fk array: a row slot (0..2N-1), the
+// partial slot fk_span + p of a split row, or the spare slot fk_span + 2G - 1.
+// Split rows are summed from their partials afterwards (fix records).
 
 // Fk holds 2N values of `real_bytes` each, padded to 16 bytes; the chunk
 // partials follow directly, so slot fk_span + c addresses them through Fk.
@@ -51,8 +47,11 @@ struct TableLayout {
     int32_t off_rspec;    // ushort4[R]: reactant species a, b, c (N = none), V index of slot 0
     int32_t off_cexp;     // real[R]: c_j = n_j + 3 (r_j - 1), so that along the profile
                           //   k_j(t) = k_j(T0, rho0) exp(-c_j t / tau)
-    int32_t off_terms;    // uint32[Q * C], chunk-major (term k of chunk c at k*Q + c)
-    int32_t off_fix;      // ushort4[n_fix]: (row, first chunk, last chunk, 0)
+    int32_t off_wsl;      // uint16[W + 1]: slice range of each warp (W = G / 32)
+    int32_t off_shdr;     // uint2[n_slices]: (base into sidx, length)
+    int32_t off_sdst;     // uint16[32 n_slices]: destination byte offsets from Fk
+    int32_t off_sidx;     // uint16[sum_s 32 len_s]: V indices, lane-interleaved
+    int32_t off_fix;      // ushort4[n_fix]: (row byte offset from Fk, first partial slot, pieces, 0)
 };
 
 // Per-group shared-memory layout (byte offsets inside one group's region).
@@ -98,7 +97,7 @@ struct PlanDev {
     const unsigned char* blob;  // device
     TableLayout tl;
     const double2* rate0;        // [R] (ln k0_j, n_j), sorted order, global: zone-load rates
-    int32_t N, R, S_r, C, Q, n_fix;
+    int32_t N, R, S_r, n_fix;
     int32_t R1, R12;             // reactions [0,R1) 1-body, [R1,R12) 2-body, [R12,R) 3-body
     double cmax;                 // max_j c_j
     int32_t zero_idx;            // V index of the constant zero (= R + S_r)
