@@ -116,27 +116,60 @@ def _peaks():
     return {"hbm_gbs": 6800.0, "bf16_tflops": 1900.0}, "fallback"
 
 
-def algorithmic_flops(net, steps, rejects, precision):
-    """Algorithmic FP64 (FP64 form) or FP32+FP64 (mixed form) operations of the
-    method per batch, counting a multiply or add as 1, an FMA as 2 and each
-    exp/div as 1, with sentinel multiplications by 1 excluded:
+def algorithmic_flops(net, steps, rejects):
+    """Algorithmic FP64 operations of the FP64 form per batch, counting a
+    multiply or add as 1, an FMA as 2 and each exp/div as 1, with sentinel
+    multiplications by 1 excluded:
       rates  5 per reaction per accepted step (2 FMA-equivalents + exp)
       fluxes+partials  1 / 3 / 7 per 1- / 2- / 3-body reaction per accepted step
-      gathers  1 per product slot and reactant slot per accepted step (+3 Kahan in mixed)
-      update+test  11 per species per attempt (accepted or rejected).
-    Returns (flops_fp64, flops_fp32)."""
+      gathers  1 per product slot and reactant slot per accepted step
+      update+test  11 per species per attempt (accepted or rejected)."""
     nr = net.n_reac
     R = net.n_reactions
     s_r, s_p = net.slot_counts()
     per_rx = np.where(nr == 1, 1, np.where(nr == 2, 3, 7)).sum()
-    rate = 5 * R
-    gather = s_r + s_p
-    upd = 11 * net.n_species
-    attempts = steps + rejects
-    if precision == "fp64":
-        return float(steps * (rate + per_rx + gather) + attempts * upd), 0.0
-    # mixed: rates (double-float, ~20 FP32 ops + ex2), fluxes and Kahan gathers in FP32
-    return float(attempts * upd), float(steps * (20 * R + per_rx + 4 * gather))
+    return float(steps * (5 * R + per_rx + s_r + s_p) + (steps + rejects) * 11 * net.n_species)
+
+
+def algorithmic_smem_bytes(net, steps, rejects):
+    """Algorithmic shared-memory bytes of the mixed form per batch: each value
+    the method reads or writes, once, in the width the mixed form keeps it.
+      flux pass, per accepted step: per reaction the reactant list (8 B), rate
+        K_j (4 B), exponent c_j (4 B) and flux store (4 B); per reactant slot the
+        abundance read (4 B) and the partial store (4 B):  20 R + 8 S_r
+      gathers, per accepted step: per term a 16-bit index and a 4 B value, per
+        row one 4 B store:  6 (S_r + S_p) + 8 N
+      update and test, per attempt: per species the abundance pair, F+, k and
+        A (20 B) read and the new pair (8 B) written:  28 N"""
+    R = net.n_reactions
+    s_r, s_p = net.slot_counts()
+    N = net.n_species
+    return float(steps * (20 * R + 8 * s_r + 6 * (s_r + s_p) + 8 * N) + (steps + rejects) * 28 * N)
+
+
+def _profile_line(name):
+    """The machine-readable line of a committed ncu summary:
+    `traffic: dram_bytes=<B> zones=<Z> sources_sha256=<H>`; (bytes, zones, hash) or None."""
+    import re
+    path = os.path.join(ROOT, "profiles", name)
+    if not os.path.exists(path):
+        return None
+    m = re.search(r"traffic: dram_bytes=(\d+) zones=(\d+) sources_sha256=([0-9a-f]+)", open(path).read())
+    return (int(m.group(1)), int(m.group(2)), m.group(3)) if m else None
+
+
+def kernel_sources_sha256():
+    """Hash of the sources that define the integrator kernel and its tables."""
+    import hashlib
+    h = hashlib.sha256()
+    for f in ("kn_integrate.cu", "kn_api.cu", "kn_internal.h"):
+        h.update(open(os.path.join(ROOT, "paper_1409_5826_gb300", "csrc", f), "rb").read())
+    return h.hexdigest()
+
+
+def _n_sms():
+    import torch
+    return torch.cuda.get_device_properties(torch.cuda.current_device()).multi_processor_count
 
 
 def run_reference(args, rank, world):
@@ -377,27 +410,46 @@ def main():
             dist.barrier()
             dist.destroy_process_group()
         return
-    f64, f32 = algorithmic_flops(net, st["steps"], st["rejects"], args.form)
     kms = float(np.mean(kern_ms))
-    peaks, src = _peaks()
-    # FP64 bound: the peak is the device's DFMA throughput measured here
-    # (the peaks file has no FP64 figure); nominal GB300 FP64 is 1.25 TFLOP/s
-    fp64_peak_tf = kn.measure_fp64_peak(stream)
     # DRAM traffic of the integrator from the committed ncu capture of this
-    # kernel (1216 zones, mixed form), scaled to this launch by zone count:
-    # each zone's state is read once per launch
-    traffic = 1.652992e6 * args.zones / 1216 if args.form == "mixed" else None
-    roof = {"bound": "alu", "unit": "TFLOP/s", "kernel": "integrate_kernel",
-            "achieved": f64 / (kms / 1e3) / 1e12, "peak": fp64_peak_tf,
-            "peak_source": "measured FP64 DFMA throughput (kn_measure_fp64_peak)", "traffic": traffic,
-            "traffic_source": "profiles/integrate_kernel_mixed_1216x150_full.md, scaled by zones"
-            if traffic else None,
-            "algorithmic_fp64_flops_per_launch": f64, "algorithmic_fp32_flops_per_launch": f32,
-            "kernel_ms": kms, "nominal_fp64_tflops": 1.25}
+    # kernel (small case, mixed form), scaled to this launch by zone count
+    # (each zone's state is read once per launch); null when the kernel's
+    # sources changed since the capture or for the FP64 form
+    prof = _profile_line("integrate_kernel_mixed_1216x150_full.md")
+    traffic = None
+    if prof and args.form == "mixed" and prof[2] == kernel_sources_sha256():
+        traffic = prof[0] * args.zones / prof[1]
+    if args.form == "mixed":
+        # SM-local bound: shared-memory bandwidth, 32 banks x 4 B per clock per
+        # SM at the SM clock sampled during the timed steps
+        sm_hz = (clk.get("sm_mhz") or 2070.0) * 1e6
+        peak = 128.0 * _n_sms() * sm_hz / 1e9
+        b = algorithmic_smem_bytes(net, st["steps"], st["rejects"])
+        roof = {"bound": "alu", "resource": "shared-memory bandwidth (SM-local)", "unit": "GB/s",
+                "kernel": "integrate_kernel", "achieved": b / (kms / 1e3) / 1e9, "peak": peak,
+                "peak_source": "derived: 128 B/clk/SM x SMs x sampled SM clock",
+                "traffic": traffic,
+                "traffic_source": "profiles/integrate_kernel_mixed_1216x150_full.md, scaled by zones"
+                if traffic else None,
+                "algorithmic_smem_bytes_per_launch": b, "kernel_ms": kms}
+    else:
+        # FP64 pipe bound: the peak is the device's DFMA throughput measured
+        # here (the peaks file has no FP64 figure); nominal 1.25 TFLOP/s
+        f64 = algorithmic_flops(net, st["steps"], st["rejects"])
+        roof = {"bound": "alu", "resource": "FP64 pipe", "unit": "TFLOP/s", "kernel": "integrate_kernel",
+                "achieved": f64 / (kms / 1e3) / 1e12, "peak": kn.measure_fp64_peak(stream),
+                "peak_source": "measured FP64 DFMA throughput (kn_measure_fp64_peak)", "traffic": None,
+                "algorithmic_fp64_flops_per_launch": f64, "kernel_ms": kms, "nominal_fp64_tflops": 1.25}
     roof["frac"] = roof["achieved"] / roof["peak"]
+    if traffic:
+        # context: the DRAM side is far from its bound
+        peaks, src = _peaks()
+        roof["dram_gbs"] = traffic / (kms / 1e3) / 1e9
+        roof["dram_frac_of_hbm"] = roof["dram_gbs"] / peaks["hbm_gbs"]
+        roof["hbm_peak_source"] = f"MEASURED_PEAKS.json hbm_gbs ({src})"
     line = {"metric": METRIC, "value": value, "unit": "zone-steps/s", "n_gpus": world, "steps": args.steps,
             "warmup": max(3, args.warmup), "ms_per_step": ms / args.steps, "higher_is_better": True,
-            "scaling": "weak", "vs_baseline": None, "dtype": "f32+f64" if args.form == "mixed" else "f64",
+            "scaling": "weak", "vs_baseline": None, "dtype": "f32 (float-float state)" if args.form == "mixed" else "f64",
             "data": "synthetic", "zones_per_s": zones_all * args.steps / (ms / 1e3),
             "config": {"workload": WORKLOAD if (args.zones, args.t_end) == (N_ZONES, T_END) else
                        f"{args.zones} zones x 150sp/1604rx, T9/rho profiles, t 1e-12 -> {args.t_end:g} s",

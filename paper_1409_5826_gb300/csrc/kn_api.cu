@@ -8,6 +8,7 @@
 #include <cstdarg>
 #include <cstdio>
 #include <cstring>
+#include <functional>
 #include <map>
 #include <memory>
 #include <string>
@@ -107,16 +108,103 @@ namespace {
 // ---------------------------------------------------------------------------
 // tables: reactant lists, rate parameters and the flat chunked gather list
 // ---------------------------------------------------------------------------
+// Bank-aware order of one slice's terms.  Step k of a slice loads
+// V[idx(k, l)] for the warp's 32 lanes l; the load takes one shared-memory
+// wavefront when the words lie in distinct banks -- the index mod 32 for
+// 4-byte values; 8-byte values take a bank pair (index mod 16), two lanes per
+// pair in one step -- or are the same word.  A lane may sum its piece in any
+// order, so each step is a maximum matching of lanes to banks (augmenting
+// paths, Kuhn's method): lanes that must take a term now to end within the
+// slice length come first, then the others by remaining terms; a lane that
+// must take a term and is not matched takes one anyway (a conflict), an
+// unmatched optional lane reads the zero entry (all such reads are one word).
+// Returns the slice length (grows only when a lane could not keep up).
+static int schedule_slice(const std::vector<std::vector<uint16_t>>& in, int len, int nbank, int cap, uint16_t zero,
+                          std::vector<std::vector<uint16_t>>& out) {
+    const int NL = (int)in.size();
+    std::vector<std::vector<uint16_t>> rem = in;
+    out.assign(NL, {});
+    const int zb = zero % nbank;
+    for (int k = 0;; ++k) {
+        int mx = 0, busy = 0;
+        for (auto& r : rem) {
+            mx = std::max(mx, (int)r.size());
+            busy += !r.empty();
+        }
+        if (mx == 0) return k;
+        const int target = std::max(len, k + mx);
+        std::vector<int> order;
+        for (int l = 0; l < NL; ++l)
+            if (!rem[l].empty()) order.push_back(l);
+        std::stable_sort(order.begin(), order.end(), [&](int x, int y) {
+            const bool mx_ = (int)rem[x].size() >= target - k, my_ = (int)rem[y].size() >= target - k;
+            if (mx_ != my_) return mx_;
+            return rem[x].size() > rem[y].size();
+        });
+        // bank slots: cap each; one slot of the zero bank is kept for padding
+        // lanes whenever some lane will pad
+        std::vector<int> cap_left(nbank, cap);
+        if (busy < NL && cap_left[zb] > 0) cap_left[zb] -= 1;
+        std::vector<std::vector<int>> holder(nbank);  // lanes matched to each bank
+        std::vector<int> match(NL, -1);
+        std::function<bool(int, std::vector<char>&)> augment = [&](int l, std::vector<char>& seen) -> bool {
+            for (uint16_t v : rem[l]) {
+                const int b = v % nbank;
+                if (seen[b]) continue;
+                seen[b] = 1;
+                if ((int)holder[b].size() < cap_left[b]) {
+                    holder[b].push_back(l);
+                    match[l] = b;
+                    return true;
+                }
+                for (size_t h = 0; h < holder[b].size(); ++h) {
+                    const int o = holder[b][h];
+                    if (augment(o, seen)) {  // o moved to another bank
+                        holder[b][h] = l;
+                        match[l] = b;
+                        return true;
+                    }
+                }
+            }
+            return false;
+        };
+        for (int l : order) {
+            std::vector<char> seen(nbank, 0);
+            augment(l, seen);
+        }
+        for (int l = 0; l < NL; ++l) {
+            uint16_t v = zero;
+            if (!rem[l].empty()) {
+                int pick = -1;
+                if (match[l] >= 0) {
+                    for (size_t t = 0; t < rem[l].size(); ++t)
+                        if (rem[l][t] % nbank == match[l]) {
+                            pick = (int)t;
+                            break;
+                        }
+                } else if ((int)rem[l].size() >= target - k) {
+                    pick = 0;  // must keep up: a conflict
+                }
+                if (pick >= 0) {
+                    v = rem[l][pick];
+                    rem[l].erase(rem[l].begin() + pick);
+                }
+            }
+            out[l].push_back(v);
+        }
+    }
+}
+
 static kn_status build_tables(kn_network* n, int prec, int Q, Tables& T) {
     const int N = n->N, R = n->R;
     const int zero_idx = R + n->S_r;
     // sorted order: position jn holds caller reaction perm[jn]; reactant slots
     // are numbered in sorted order too
-    std::vector<int> sslot0(R);
-    for (int jn = 0, s0 = 0; jn < R; ++jn) {
-        sslot0[jn] = s0;
-        s0 += n->nr[n->perm[jn]];
-    }
+    // reactant-slot partials in planes: partial q of reaction jn at
+    // plane_base(q) + jn, plane q holding the reactions with more than q
+    // reactants (V = [fluxes R | plane 0: R | plane 1: R - R1 | plane 2: R - R12 | 0])
+    const int R1 = n->R1, R12 = n->R12;
+    const int plane_base[3] = {R, 2 * R - R1, 3 * R - R1 - R12};
     // rows 0..N-1: F+_i (value index jn, once per product slot naming i);
     // rows N..2N-1: k_i (value index R + reactant slot id naming i)
     std::vector<std::vector<uint16_t>> rows(2 * N);
@@ -126,7 +214,7 @@ static kn_status build_tables(kn_network* n, int prec, int Q, Tables& T) {
             const int p = n->prod[j * 3 + q];
             if (p >= 0) rows[p].push_back((uint16_t)jn);
         }
-        for (int q = 0; q < n->nr[j]; ++q) rows[N + n->reac[j * 3 + q]].push_back((uint16_t)(R + sslot0[jn] + q));
+        for (int q = 0; q < n->nr[j]; ++q) rows[N + n->reac[j * 3 + q]].push_back((uint16_t)(plane_base[q] + jn));
     }
     for (int r = 0; r < 2 * N; ++r)
         if (rows[r].empty()) rows[r].push_back((uint16_t)zero_idx);  // row written as 0
@@ -212,16 +300,20 @@ static kn_status build_tables(kn_network* n, int prec, int Q, Tables& T) {
     for (int w = 0; w < W; ++w) {
         wsl[w] = (uint16_t)n_slices;
         for (int s : best.warp_slices[w]) {
-            const int len = best.slice_len[s];
+            std::vector<std::vector<uint16_t>> lanes(32), ordered;
+            for (int l = 0; l < 32; ++l) {
+                const Piece& pc = best.pieces[32 * s + l];
+                sdst.push_back((uint16_t)pc.dst);
+                for (int k = 0; k < pc.len; ++k) lanes[l].push_back(rows[pc.row][pc.start + k]);
+            }
+            const int len = schedule_slice(lanes, best.slice_len[s], real_bytes == 4 ? 32 : 16,
+                                           real_bytes == 4 ? 1 : 2, (uint16_t)zero_idx, ordered);
             shdr.push_back((uint32_t)sidx.size());
             shdr.push_back((uint32_t)len);
             const size_t base = sidx.size();
             sidx.resize(base + 32 * (size_t)len, (uint16_t)zero_idx);
-            for (int l = 0; l < 32; ++l) {
-                const Piece& pc = best.pieces[32 * s + l];
-                sdst.push_back((uint16_t)pc.dst);
-                for (int k = 0; k < pc.len; ++k) sidx[base + 32 * (size_t)k + l] = rows[pc.row][pc.start + k];
-            }
+            for (int l = 0; l < 32; ++l)
+                for (int k = 0; k < len; ++k) sidx[base + 32 * (size_t)k + l] = ordered[l][k];
             ++n_slices;
         }
     }
@@ -262,7 +354,7 @@ static kn_status build_tables(kn_network* n, int prec, int Q, Tables& T) {
         rs[0] = (uint16_t)n->reac[j * 3];
         rs[1] = (uint16_t)(n->nr[j] >= 2 ? n->reac[j * 3 + 1] : N);
         rs[2] = (uint16_t)(n->nr[j] >= 3 ? n->reac[j * 3 + 2] : N);
-        rs[3] = (uint16_t)(R + sslot0[jn]);
+        rs[3] = 0;
         memcpy(blob.data() + tl.off_rspec + 8 * jn, rs, 8);
         const double c = n->tn[j] + 3.0 * (n->nr[j] - 1);
         if (prec == kPrecFP64) {
@@ -701,16 +793,18 @@ static kn_status prepare_launch(kn_network* const* nets, int n_nets, const kn_op
         }
         if (!P_best && n_nets == 1 && !o->threads_per_cta) {
             // one network, no explicit CTA size, tables staged in shared memory.
-            // Single-warp groups (small networks): the most groups per CTA,
-            // which hides their short serial sections behind one another.
-            // Larger groups: up to kTargetGroups groups, then the largest group
-            // (shorter gather chunks); measured on the 150-species network,
-            // 5 x 192 beats 6 x 160, 5 x 160 and 3 x 320 threads.
+            // FP64 form, and single-warp groups (small networks): the most
+            // groups per CTA, then the smallest group -- the FP64 pipe, or the
+            // groups' short serial sections, are best shared by many groups.
+            // Mixed form with larger groups: up to kTargetGroups groups, then
+            // the largest group (fewer gather slices per warp); measured on the
+            // 150-species network, mixed 5 x 192 beats 6 x 160, 5 x 160 and
+            // 3 x 320 threads, while FP64 3 x 128 beats 3 x 320.
             kn_network* n = nets[0];
             Tiling best;
             const int g0 = o->threads_per_zone ? o->threads_per_zone : base_group(n);
             const int g1 = o->threads_per_zone ? o->threads_per_zone : 512;
-            const bool small = g0 == 32;
+            const bool small = g0 == 32 || prec == kPrecFP64;
             constexpr int kTargetGroups = 5;
             for (int G = g0; G <= g1; G += 32) {
                 Tables* tb;

@@ -473,12 +473,16 @@ __device__ float mlp_forward_group(const OptsDev& O, const GroupPtrs& g, const u
 
 // Mixed form, one reactant-count class of the sorted reactions: reactions
 // j, j + stride, ... below j_end; returns the first index at or past j_end,
-// where the next class continues.  VAR: k_j(t) = K_j 2^(-c_j u).
+// where the next class continues.  VAR: k_j(t) = K_j 2^(-c_j u).  The flux
+// goes to V[j] and partial q (the product of k_j and the other reactants'
+// abundances) to plane q at Pq[j], so a warp's stores are contiguous.
 template <bool VAR, int NB>
 __device__ __forceinline__ int flux_class(int j, int j_end, int stride, const ushort4* __restrict__ rspec,
                                           const float* __restrict__ cexp, const float* __restrict__ Kz,
-                                          const float* __restrict__ Y, float* __restrict__ V, float u) {
-#pragma unroll 2
+                                          const float* __restrict__ Y, float* __restrict__ V,
+                                          float* __restrict__ P0, float* __restrict__ P1, float* __restrict__ P2,
+                                          float u) {
+#pragma unroll 1
     for (; j < j_end; j += stride) {
         const ushort4 rs = rspec[j];
         float k = Kz[j];
@@ -486,19 +490,19 @@ __device__ __forceinline__ int flux_class(int j, int j_end, int stride, const us
         const float ya = Y[rs.x];
         if (NB == 1) {
             V[j] = __fmul_rn(k, ya);
-            V[rs.w] = k;
+            P0[j] = k;
         } else if (NB == 2) {
             const float yb = Y[rs.y];
             V[j] = __fmul_rn(__fmul_rn(k, ya), yb);
-            V[rs.w] = __fmul_rn(k, yb);
-            V[rs.w + 1] = __fmul_rn(k, ya);
+            P0[j] = __fmul_rn(k, yb);
+            P1[j] = __fmul_rn(k, ya);
         } else {
             const float yb = Y[rs.y], yc = Y[rs.z];
             const float ka = __fmul_rn(k, ya);
             V[j] = __fmul_rn(__fmul_rn(ka, yb), yc);
-            V[rs.w] = __fmul_rn(__fmul_rn(k, yb), yc);
-            V[rs.w + 1] = __fmul_rn(ka, yc);
-            V[rs.w + 2] = __fmul_rn(ka, yb);
+            P0[j] = __fmul_rn(__fmul_rn(k, yb), yc);
+            P1[j] = __fmul_rn(ka, yc);
+            P2[j] = __fmul_rn(ka, yb);
         }
     }
     return j;
@@ -517,6 +521,7 @@ __device__ __forceinline__ void flux_pass(const PlanDev& P, const GroupPtrs& g, 
     const real* __restrict__ cexp = (const real*)g.cexp;
     const real* __restrict__ Kz = (const real*)g.K;
     real* __restrict__ Vw = (real*)g.V;
+    const int pb1 = 2 * R - R1, pb2 = 3 * R - R1 - R12;  // bases of partial planes 1 and 2
     if (PREC == kPrecFP64) {
         const double* __restrict__ Yr = g.Y64 + buf * NP1;
 #pragma unroll 2
@@ -530,19 +535,19 @@ __device__ __forceinline__ void flux_pass(const PlanDev& P, const GroupPtrs& g, 
             const double ya = Yr[rs.x];
             if (j < R1) {
                 Vw[j] = (real)(k * ya);
-                Vw[rs.w] = (real)k;
+                Vw[R + j] = (real)k;
             } else if (j < R12) {
                 const double yb = Yr[rs.y];
                 Vw[j] = (real)(k * ya * yb);
-                Vw[rs.w] = (real)(k * yb);
-                Vw[rs.w + 1] = (real)(k * ya);
+                Vw[R + j] = (real)(k * yb);
+                Vw[pb1 + j] = (real)(k * ya);
             } else {
                 const double yb = Yr[rs.y], yc = Yr[rs.z];
                 const double ka = k * ya;
                 Vw[j] = (real)(ka * yb * yc);
-                Vw[rs.w] = (real)(k * yb * yc);
-                Vw[rs.w + 1] = (real)(ka * yc);
-                Vw[rs.w + 2] = (real)(ka * yb);
+                Vw[R + j] = (real)(k * yb * yc);
+                Vw[pb1 + j] = (real)(ka * yc);
+                Vw[pb2 + j] = (real)(ka * yb);
             }
         }
     } else {
@@ -550,14 +555,17 @@ __device__ __forceinline__ void flux_pass(const PlanDev& P, const GroupPtrs& g, 
         const float* __restrict__ cf = (const float*)g.cexp;
         const float* __restrict__ Kf = (const float*)g.K;
         float* __restrict__ Vf = (float*)g.V;
+        float* P0 = Vf + R;
+        float* P1 = Vf + pb1;
+        float* P2 = Vf + pb2;
         if (constant) {
-            int j = flux_class<false, 1>(j0, R1, stride, rspec, cf, Kf, Yc32, Vf, u);
-            j = flux_class<false, 2>(j, R12, stride, rspec, cf, Kf, Yc32, Vf, u);
-            flux_class<false, 3>(j, R, stride, rspec, cf, Kf, Yc32, Vf, u);
+            int j = flux_class<false, 1>(j0, R1, stride, rspec, cf, Kf, Yc32, Vf, P0, P1, P2, u);
+            j = flux_class<false, 2>(j, R12, stride, rspec, cf, Kf, Yc32, Vf, P0, P1, P2, u);
+            flux_class<false, 3>(j, R, stride, rspec, cf, Kf, Yc32, Vf, P0, P1, P2, u);
         } else {
-            int j = flux_class<true, 1>(j0, R1, stride, rspec, cf, Kf, Yc32, Vf, u);
-            j = flux_class<true, 2>(j, R12, stride, rspec, cf, Kf, Yc32, Vf, u);
-            flux_class<true, 3>(j, R, stride, rspec, cf, Kf, Yc32, Vf, u);
+            int j = flux_class<true, 1>(j0, R1, stride, rspec, cf, Kf, Yc32, Vf, P0, P1, P2, u);
+            j = flux_class<true, 2>(j, R12, stride, rspec, cf, Kf, Yc32, Vf, P0, P1, P2, u);
+            flux_class<true, 3>(j, R, stride, rspec, cf, Kf, Yc32, Vf, P0, P1, P2, u);
         }
     }
 }

@@ -44,7 +44,7 @@ constexpr int kMlpSmemBytes = (kMlpFeatures * kMlpHidden + kMlpHidden * kMlpHidd
 struct TableLayout {
     int32_t bytes;        // total (multiple of 16)
     int32_t off_A;        // real[N] (mass numbers; integers, exact in FP32)
-    int32_t off_rspec;    // ushort4[R]: reactant species a, b, c (N = none), V index of slot 0
+    int32_t off_rspec;    // ushort4[R]: reactant species a, b, c (N = none), 0
     int32_t off_cexp;     // real[R]: c_j = n_j + 3 (r_j - 1), so that along the profile
                           //   k_j(t) = k_j(T0, rho0) exp(-c_j t / tau)
     int32_t off_wsl;      // uint16[W + 1]: slice range of each warp (W = G / 32)
@@ -57,7 +57,8 @@ struct TableLayout {
 // Per-group shared-memory layout (byte offsets inside one group's region).
 struct GroupLayout {
     int32_t bytes;
-    int32_t off_V;      // real[R + S_r + 1]: fluxes, reactant-slot partials, constant 0
+    int32_t off_V;      // real[R + S_r + 1]: fluxes f_j, partial planes 0, 1, 2 (reactions with
+                        //   more than 0, 1, 2 reactants), constant 0
     int32_t off_K;      // real[R]: the zone's rates at (T0, rho0)
     int32_t off_Y;      // FP64: double[2][N + 1], entry N the constant 1; mixed: float[2][N + 1],
                         //   the low parts of the float-float abundances (0 at entry N)
