@@ -586,6 +586,53 @@ kn_status kn_create_network(const kn_network_desc* d, kn_network** out) {
         n->R1 += n->nr[j] == 1;
         n->R12 += n->nr[j] <= 2;
     }
+    // Within each class, a warp of the flux pass handles an aligned block of
+    // 32 consecutive sorted reactions and loads reactant q's abundance for
+    // each; the loads are one wavefront when the species lie in distinct
+    // banks (species mod 32) or coincide.  Greedy order: each position of a
+    // block takes the remaining reaction of its class that adds the fewest
+    // bank conflicts with what the block already reads, per operand.
+    {
+        const int bounds[4] = {0, n->R1, n->R12, R};
+        std::vector<int> sorted(n->perm);
+        for (int cls = 0; cls < 3; ++cls) {
+            std::vector<int> pool(sorted.begin() + bounds[cls], sorted.begin() + bounds[cls + 1]);
+            std::vector<char> used(pool.size(), 0);
+            int block = -1;
+            // distinct species the block reads per (operand, bank)
+            std::vector<std::vector<std::vector<int>>> words(3, std::vector<std::vector<int>>(32));
+            for (int pos = bounds[cls]; pos < bounds[cls + 1]; ++pos) {
+                if (pos / 32 != block) {
+                    block = pos / 32;
+                    for (auto& wq : words)
+                        for (auto& wb : wq) wb.clear();
+                }
+                int best = -1, best_cost = 1 << 30;
+                for (size_t c = 0; c < pool.size() && best_cost > 0; ++c) {
+                    if (used[c]) continue;
+                    const int j = pool[c];
+                    int cost = 0;
+                    for (int q = 0; q < n->nr[j]; ++q) {
+                        const int sp = n->reac[j * 3 + q];
+                        const auto& wb = words[q][sp % 32];
+                        cost += !wb.empty() && std::find(wb.begin(), wb.end(), sp) == wb.end();
+                    }
+                    if (cost < best_cost) {
+                        best_cost = cost;
+                        best = (int)c;
+                    }
+                }
+                used[best] = 1;
+                const int j = pool[best];
+                n->perm[pos] = j;
+                for (int q = 0; q < n->nr[j]; ++q) {
+                    const int sp = n->reac[j * 3 + q];
+                    auto& wb = words[q][sp % 32];
+                    if (std::find(wb.begin(), wb.end(), sp) == wb.end()) wb.push_back(sp);
+                }
+            }
+        }
+    }
     std::vector<double> r0(2 * (size_t)R);
     for (int jn = 0; jn < R; ++jn) {
         const int j = n->perm[jn];
