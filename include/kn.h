@@ -38,7 +38,9 @@ typedef enum {
     KN_ERR_INVALID_ARG = 1, /* bad pointer, size, value or layout */
     KN_ERR_CUDA = 2,        /* a CUDA runtime call failed (message has the CUDA error) */
     KN_ERR_NOMEM = 3,       /* device or host allocation failed */
-    KN_ERR_STATE = 4        /* call out of order (e.g. integrate before zones are set) */
+    KN_ERR_STATE = 4,       /* call out of order (e.g. integrate before zones are set) */
+    KN_ERR_INTERNAL = 5     /* a self-check of the library failed before any device work
+                               (a bug; the message names the check) */
 } kn_status;
 
 /* Per-zone outcome, written by kn_integrate_batch. */
@@ -56,8 +58,12 @@ typedef enum { KN_MEM_HOST = 0, KN_MEM_DEVICE = 1 } kn_mem;
 
 typedef enum {
     KN_PREC_FP64 = 0, /* every step of the path in FP64 */
-    KN_PREC_MIXED = 1 /* FP32 rates and fluxes, Kahan-compensated FP32 gathers,
-                         FP64 update, conservation sum and error test */
+    KN_PREC_MIXED = 1 /* FP32 rates, fluxes and gathers (every row sum of positive
+                         terms within (L + 5) 2^-24 relative, L <= the longest row);
+                         abundances kept as FP32 high/low pairs (~48 bits); the
+                         kappa-switched update in FP32; the conservation sum as a
+                         float-float sum of exact products; the relative-error
+                         test in FP32 outside a guard band, FP64 inside it */
 } kn_precision;
 
 /*
@@ -192,6 +198,21 @@ kn_status kn_destroy_network(kn_network *net);
    (any pointer may be NULL). */
 kn_status kn_network_info(const kn_network *net, int32_t *n_species, int32_t *n_reactions,
                           int32_t *n_reactant_slots, int32_t *n_product_slots);
+
+/*
+ * Host-only check of the gather tables the integrator would use for this
+ * description at `precision` with zone groups of `threads_per_zone` threads
+ * (a multiple of 32 in [32, 1024]); no device is touched.  The F+ and k sums
+ * of Eq. 1 (Sec. 10 item (2)) are laid out as warp slices of row pieces; the
+ * builder verifies every index and destination and, running the gather on
+ * the host with V[v] = v + 1, that every row's sum comes out exactly once.
+ * stats (4 int32, caller-owned) receives: the piece length cap L, the number
+ * of slices, the longest warp's terms per lane, and the table bytes.
+ * Errors: KN_ERR_INVALID_ARG (as kn_create_network, or a bad precision or
+ * group size), KN_ERR_INTERNAL (a table check failed; the message names it).
+ */
+kn_status kn_check_gather_tables(const kn_network_desc *desc, int32_t precision, int32_t threads_per_zone,
+                                 int32_t stats[4]);
 
 /*
  * Load n_zones zones into the network's device state (Sec. 6, step 1: the

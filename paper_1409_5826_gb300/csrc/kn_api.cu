@@ -76,7 +76,6 @@ struct DevBuf {
 struct Tables {
     std::unique_ptr<DevBuf> blob;
     TableLayout tl{};
-    int n_fix = 0;
     int L = 0, n_slices = 0, warp_len = 0;  // piece cap, slices, longest warp's terms per lane
 };
 }  // namespace kn
@@ -195,7 +194,10 @@ static int schedule_slice(const std::vector<std::vector<uint16_t>>& in, int len,
     }
 }
 
-static kn_status build_tables(kn_network* n, int prec, int Q, Tables& T) {
+// The tables of one network for (precision, threads per zone group Q), built
+// and checked on the host; `blob` is what goes to the device.
+static kn_status build_tables_host(const kn_network* n, int prec, int Q, std::vector<unsigned char>& blob,
+                                   Tables& T) {
     const int N = n->N, R = n->R;
     const int zero_idx = R + n->S_r;
     // sorted order: position jn holds caller reaction perm[jn]; reactant slots
@@ -221,64 +223,86 @@ static kn_status build_tables(kn_network* n, int prec, int Q, Tables& T) {
     const int real_bytes = prec == kPrecFP64 ? 8 : 4;
     const int fspan = fk_span(N, real_bytes);
     const int G = Q, W = G / 32;
-    const int spare = fspan + 2 * G - 1;
+    const int spare = fspan;  // padding lanes store here
     if ((spare + 1) * real_bytes > 0xffff) return fail(KN_ERR_INVALID_ARG, "network too large for the gather tables");
     size_t maxlen = 0;
     for (auto& r : rows) maxlen = std::max(maxlen, r.size());
-    // One layout for a piece cap L: pieces, slices, and the slices' warps
-    // (longest-first onto the least-loaded warp).  Its cost is the longest
-    // warp's terms per lane plus the longest fix-up.
+    // One layout for a piece cap L.  A row of more than L terms is cut into
+    // k = ceil(len / L) pieces placed in k consecutive lanes of one slice
+    // (k <= 32), whose sums a segmented warp reduction combines.  Units
+    // (rows) in order of piece length fill slices: a slice opens with the
+    // longest remaining unit and takes every later unit that still fits its
+    // lanes.  Slices go longest-first to the least-loaded warp; the cost is
+    // the longest warp's load, a term counting 1 and the segmented reduction
+    // of a slice with split rows kSegCost (its five shuffle rounds take about
+    // as many instructions as that many terms).
     struct Piece {
         int row, start, len, dst;
     };
+    struct Unit {
+        int row, k, plen;
+    };
     struct Layout {
-        std::vector<Piece> pieces;
-        std::vector<uint16_t> fix;
-        std::vector<std::vector<int>> warp_slices;  // slice ids per warp
+        std::vector<std::vector<Piece>> slices;  // 32 pieces each
+        std::vector<char> seg;                   // the slice holds a split row
+        std::vector<std::vector<int>> warp_slices;
         std::vector<int> slice_len;
-        int cost = 1 << 30, warp_len = 0;
+        int cost = 1 << 30, warp_len = 0, n_split = 0;
     };
     auto layout_for = [&](int L, Layout& out) -> bool {
         Layout lo;
-        int n_part = 0, max_fix = 0;
+        std::vector<Unit> units;
         for (int r = 0; r < 2 * N; ++r) {
             const int len = (int)rows[r].size();
-            if (len <= L) {
-                lo.pieces.push_back({r, 0, len, r * real_bytes});
-                continue;
-            }
-            const int np = (len + L - 1) / L;
-            lo.fix.push_back((uint16_t)(r * real_bytes));
-            lo.fix.push_back((uint16_t)n_part);
-            lo.fix.push_back((uint16_t)np);
-            lo.fix.push_back(0);
-            for (int q = 0, st = 0; q < np; ++q) {
-                const int pl = len / np + (q < len % np ? 1 : 0);
-                lo.pieces.push_back({r, st, pl, (fspan + n_part) * real_bytes});
-                st += pl;
-                ++n_part;
-            }
-            max_fix = std::max(max_fix, np);
+            const int k = (len + L - 1) / L;
+            if (k > 32) return false;
+            units.push_back({r, k, (len + k - 1) / k});
+            lo.n_split += k > 1;
         }
-        if (n_part > 2 * G - 1) return false;  // partials and the spare share the 2G carry slots
-        std::stable_sort(lo.pieces.begin(), lo.pieces.end(),
-                         [](const Piece& x, const Piece& y) { return x.len > y.len; });
-        while (lo.pieces.size() % 32) lo.pieces.push_back({-1, 0, 0, spare * real_bytes});
-        const int ns = (int)lo.pieces.size() / 32;
-        for (int s = 0; s < ns; ++s) lo.slice_len.push_back(lo.pieces[32 * s].len);
-        std::vector<int> order(ns);
-        for (int s = 0; s < ns; ++s) order[s] = s;
-        std::stable_sort(order.begin(), order.end(),
-                         [&](int x, int y) { return lo.slice_len[x] > lo.slice_len[y]; });
+        std::stable_sort(units.begin(), units.end(), [](const Unit& x, const Unit& y) { return x.plen > y.plen; });
+        std::vector<char> taken(units.size(), 0);
+        size_t first = 0;
+        for (;;) {
+            while (first < units.size() && taken[first]) ++first;
+            if (first == units.size()) break;
+            std::vector<Piece> sl;
+            char seg = 0;
+            for (size_t u = first; u < units.size() && sl.size() < 32; ++u) {
+                if (taken[u] || (int)sl.size() + units[u].k > 32) continue;
+                taken[u] = 1;
+                const int r = units[u].row, len = (int)rows[r].size(), k = units[u].k;
+                seg |= k > 1;
+                for (int q = 0, st = 0; q < k; ++q) {
+                    const int pl = len / k + (q < len % k ? 1 : 0);
+                    sl.push_back({r, st, pl, r * real_bytes});
+                    st += pl;
+                }
+            }
+            while (sl.size() < 32) sl.push_back({-1, 0, 0, spare * real_bytes});
+            int sl_len = 0;
+            for (auto& pc : sl) sl_len = std::max(sl_len, pc.len);
+            lo.slice_len.push_back(sl_len);
+            lo.seg.push_back(seg);
+            lo.slices.push_back(std::move(sl));
+        }
+        constexpr int kSegCost = 6;
+        const int ns = (int)lo.slices.size();
+        std::vector<int> order(ns), cost(ns);
+        for (int s = 0; s < ns; ++s) {
+            order[s] = s;
+            cost[s] = lo.slice_len[s] + (lo.seg[s] ? kSegCost : 0);
+        }
+        std::stable_sort(order.begin(), order.end(), [&](int x, int y) { return cost[x] > cost[y]; });
         lo.warp_slices.assign(W, {});
-        std::vector<int> load(W, 0);
+        std::vector<int> load(W, 0), terms(W, 0);
         for (int s : order) {
             const int w = (int)(std::min_element(load.begin(), load.end()) - load.begin());
             lo.warp_slices[w].push_back(s);
-            load[w] += lo.slice_len[s];
+            load[w] += cost[s];
+            terms[w] += lo.slice_len[s];
         }
-        lo.warp_len = *std::max_element(load.begin(), load.end());
-        lo.cost = lo.warp_len + 2 * max_fix;
+        lo.warp_len = *std::max_element(terms.begin(), terms.end());
+        lo.cost = *std::max_element(load.begin(), load.end());
         out = std::move(lo);
         return true;
     };
@@ -287,13 +311,13 @@ static kn_status build_tables(kn_network* n, int prec, int Q, Tables& T) {
     for (int L = 1; L <= (int)maxlen; ++L) {
         Layout lo;
         if (!layout_for(L, lo)) continue;
-        if (lo.cost < best.cost || (lo.cost == best.cost && lo.fix.size() <= best.fix.size())) {
+        if (lo.cost < best.cost || (lo.cost == best.cost && lo.n_split < best.n_split)) {
             best = std::move(lo);
             L_best = L;
         }
     }
     if (!L_best) return fail(KN_ERR_INVALID_ARG, "no gather layout fits %d threads per zone", G);
-    // flatten: slices in warp order
+    // flatten: slices in warp order; header (base into sidx, length | split flag << 31)
     std::vector<uint16_t> wsl(W + 1, 0), sdst, sidx;
     std::vector<uint32_t> shdr;
     int n_slices = 0;
@@ -302,14 +326,14 @@ static kn_status build_tables(kn_network* n, int prec, int Q, Tables& T) {
         for (int s : best.warp_slices[w]) {
             std::vector<std::vector<uint16_t>> lanes(32), ordered;
             for (int l = 0; l < 32; ++l) {
-                const Piece& pc = best.pieces[32 * s + l];
+                const Piece& pc = best.slices[s][l];
                 sdst.push_back((uint16_t)pc.dst);
                 for (int k = 0; k < pc.len; ++k) lanes[l].push_back(rows[pc.row][pc.start + k]);
             }
             const int len = schedule_slice(lanes, best.slice_len[s], real_bytes == 4 ? 32 : 16,
                                            real_bytes == 4 ? 1 : 2, (uint16_t)zero_idx, ordered);
             shdr.push_back((uint32_t)sidx.size());
-            shdr.push_back((uint32_t)len);
+            shdr.push_back((uint32_t)len | (best.seg[s] ? 0x80000000u : 0u));
             const size_t base = sidx.size();
             sidx.resize(base + 32 * (size_t)len, (uint16_t)zero_idx);
             for (int l = 0; l < 32; ++l)
@@ -318,7 +342,47 @@ static kn_status build_tables(kn_network* n, int prec, int Q, Tables& T) {
         }
     }
     wsl[W] = (uint16_t)n_slices;
-    const std::vector<uint16_t>& fix = best.fix;
+    // Host check of the tables before they reach a device: every index in
+    // range, a split row's pieces in consecutive lanes of a flagged slice, and
+    // the gather, run on the host with V[v] = v + 1, giving every row's sum
+    // exactly once (integer sums, exact in FP64).
+    {
+        std::vector<double> got(2 * N, -1.0);
+        for (int w = 0; w < W; ++w)
+            for (int sl = wsl[w]; sl < wsl[w + 1]; ++sl) {
+                const uint32_t base = shdr[2 * sl], len = shdr[2 * sl + 1] & 0x7fffffffu;
+                const bool seg = (shdr[2 * sl + 1] >> 31) != 0;
+                if (base + 32 * (size_t)len > sidx.size()) return fail(KN_ERR_INTERNAL, "gather table: slice out of range");
+                double acc[32];
+                for (int l = 0; l < 32; ++l) {
+                    acc[l] = 0.0;
+                    for (uint32_t k = 0; k < len; ++k) {
+                        const uint16_t v = sidx[base + 32 * k + l];
+                        if (v > zero_idx) return fail(KN_ERR_INTERNAL, "gather table: value index out of range");
+                        acc[l] += v == zero_idx ? 0.0 : (double)v + 1.0;
+                    }
+                }
+                for (int l = 0; l < 32;) {
+                    const uint16_t d = sdst[32 * sl + l];
+                    int e = l + 1;
+                    double sum = acc[l];
+                    while (e < 32 && sdst[32 * sl + e] == d) sum += acc[e++];
+                    if (d % real_bytes || d / real_bytes > spare) return fail(KN_ERR_INTERNAL, "gather table: bad destination");
+                    const int r = d / real_bytes;
+                    if (r < 2 * N) {
+                        if (e - l > 1 && !seg) return fail(KN_ERR_INTERNAL, "gather table: split row in an unflagged slice");
+                        if (got[r] >= 0.0) return fail(KN_ERR_INTERNAL, "gather table: row %d stored twice", r);
+                        got[r] = sum;
+                    }
+                    l = e;
+                }
+            }
+        for (int r = 0; r < 2 * N; ++r) {
+            double want = 0.0;
+            for (uint16_t v : rows[r]) want += v == zero_idx ? 0.0 : (double)v + 1.0;
+            if (got[r] != want) return fail(KN_ERR_INTERNAL, "gather table: row %d sums to %g, not %g", r, got[r], want);
+        }
+    }
     const int real = prec == kPrecFP64 ? 8 : 4;
     TableLayout tl{};
     int off = 0;
@@ -336,10 +400,8 @@ static kn_status build_tables(kn_network* n, int prec, int Q, Tables& T) {
     off = pad16(off + 2 * (int)sdst.size());
     tl.off_sidx = off;
     off = pad16(off + 2 * (int)sidx.size());
-    tl.off_fix = off;
-    off = pad16(off + 2 * (int)fix.size());
     tl.bytes = off;
-    std::vector<unsigned char> blob(off, 0);
+    blob.assign(off, 0);
     for (int i = 0; i < N; ++i) {
         if (prec == kPrecFP64) {
             memcpy(blob.data() + tl.off_A + 8 * i, &n->A[i], 8);
@@ -368,15 +430,20 @@ static kn_status build_tables(kn_network* n, int prec, int Q, Tables& T) {
     memcpy(blob.data() + tl.off_shdr, shdr.data(), 4 * shdr.size());
     memcpy(blob.data() + tl.off_sdst, sdst.data(), 2 * sdst.size());
     memcpy(blob.data() + tl.off_sidx, sidx.data(), 2 * sidx.size());
-    if (!fix.empty()) memcpy(blob.data() + tl.off_fix, fix.data(), 2 * fix.size());
-    T.blob.reset(new DevBuf());
-    KN_CUDA(T.blob->ensure(off));
-    KN_CUDA(cudaMemcpy(T.blob->p, blob.data(), off, cudaMemcpyHostToDevice));
     T.tl = tl;
-    T.n_fix = (int)fix.size() / 4;
     T.L = L_best;
     T.n_slices = n_slices;
     T.warp_len = best.warp_len;
+    return KN_OK;
+}
+
+static kn_status build_tables(kn_network* n, int prec, int Q, Tables& T) {
+    std::vector<unsigned char> blob;
+    kn_status s = build_tables_host(n, prec, Q, blob, T);
+    if (s != KN_OK) return s;
+    T.blob.reset(new DevBuf());
+    KN_CUDA(T.blob->ensure(blob.size()));
+    KN_CUDA(cudaMemcpy(T.blob->p, blob.data(), blob.size(), cudaMemcpyHostToDevice));
     return KN_OK;
 }
 
@@ -408,7 +475,7 @@ static GroupLayout group_layout(const kn_network* n, int prec, int G, bool feat)
     g.off_Fk = off;
     off = pad16(off + real * 2 * n->N);
     g.off_carry = off;
-    off = pad16(off + real * 2 * G);
+    off = pad16(off + real);
     g.off_red = off;
     off = pad16(off + (G / 32) * (8 * 3 + 4 + 4));
     g.off_feat = off;
@@ -525,15 +592,16 @@ void kn_default_opts(kn_opts* o) {
 
 const char* kn_last_error(void) { return g_err.c_str(); }
 
-kn_status kn_create_network(const kn_network_desc* d, kn_network** out) {
-    if (!d || !out) return fail(KN_ERR_INVALID_ARG, "kn_create_network: NULL argument");
-    *out = nullptr;
+// Validation, the sorted reaction order and the host-side network data; no
+// device work.
+static kn_status network_host_setup(const kn_network_desc* d, std::unique_ptr<kn_network>& n,
+                                    std::vector<double>& r0) {
     const int N = d->n_species, R = d->n_reactions;
     if (N < 1 || N > kMaxSpecies) return fail(KN_ERR_INVALID_ARG, "n_species %d outside [1, %d]", N, kMaxSpecies);
     if (R < 1 || R > 16383) return fail(KN_ERR_INVALID_ARG, "n_reactions %d outside [1, 16383]", R);
     if (!d->A || !d->reac || !d->prod || !d->ln_k0 || !d->t9_exp)
         return fail(KN_ERR_INVALID_ARG, "kn_network_desc has a NULL array");
-    std::unique_ptr<kn_network> n(new kn_network());
+    n.reset(new kn_network());
     n->N = N;
     n->R = R;
     n->A.assign(d->A, d->A + N);
@@ -633,20 +701,52 @@ kn_status kn_create_network(const kn_network_desc* d, kn_network** out) {
             }
         }
     }
-    std::vector<double> r0(2 * (size_t)R);
+    r0.assign(2 * (size_t)R, 0.0);
     for (int jn = 0; jn < R; ++jn) {
         const int j = n->perm[jn];
         r0[2 * jn] = n->lnk0[j];
         r0[2 * jn + 1] = n->tn[j];
         n->cmax = std::max(n->cmax, std::fabs(n->tn[j] + 3.0 * (n->nr[j] - 1)));
     }
-    KN_CUDA(n->rate0.ensure(16 * (size_t)R));
-    KN_CUDA(cudaMemcpy(n->rate0.p, r0.data(), 16 * (size_t)R, cudaMemcpyHostToDevice));
     if (R + slots + 1 > 0xffff) return fail(KN_ERR_INVALID_ARG, "network too large for 16-bit gather indices");
     n->nbar = nsum / R;
     n->rbar = rsum / R;
+    return KN_OK;
+}
+
+kn_status kn_create_network(const kn_network_desc* d, kn_network** out) {
+    if (!d || !out) return fail(KN_ERR_INVALID_ARG, "kn_create_network: NULL argument");
+    *out = nullptr;
+    std::unique_ptr<kn_network> n;
+    std::vector<double> r0;
+    kn_status s = network_host_setup(d, n, r0);
+    if (s != KN_OK) return s;
+    KN_CUDA(n->rate0.ensure(8 * r0.size()));
+    KN_CUDA(cudaMemcpy(n->rate0.p, r0.data(), 8 * r0.size(), cudaMemcpyHostToDevice));
     KN_CUDA(n->qhead.ensure(64));
     *out = n.release();
+    return KN_OK;
+}
+
+kn_status kn_check_gather_tables(const kn_network_desc* d, int32_t precision, int32_t threads_per_zone,
+                                 int32_t stats[4]) {
+    if (!d || !stats) return fail(KN_ERR_INVALID_ARG, "kn_check_gather_tables: NULL argument");
+    if (precision != KN_PREC_FP64 && precision != KN_PREC_MIXED)
+        return fail(KN_ERR_INVALID_ARG, "kn_check_gather_tables: bad precision");
+    if (threads_per_zone < 32 || threads_per_zone > 1024 || threads_per_zone % 32)
+        return fail(KN_ERR_INVALID_ARG, "kn_check_gather_tables: threads_per_zone must be a multiple of 32 in [32, 1024]");
+    std::unique_ptr<kn_network> n;
+    std::vector<double> r0;
+    kn_status s = network_host_setup(d, n, r0);
+    if (s != KN_OK) return s;
+    std::vector<unsigned char> blob;
+    Tables T;
+    s = build_tables_host(n.get(), precision, threads_per_zone, blob, T);
+    if (s != KN_OK) return s;
+    stats[0] = T.L;
+    stats[1] = T.n_slices;
+    stats[2] = T.warp_len;
+    stats[3] = (int)blob.size();
     return KN_OK;
 }
 
@@ -908,7 +1008,6 @@ static kn_status prepare_launch(kn_network* const* nets, int n_nets, const kn_op
         P.N = n->N;
         P.R = n->R;
         P.S_r = n->S_r;
-        P.n_fix = tb->n_fix;
         P.zero_idx = n->R + n->S_r;
         P.smem_tables = t.smem_tables;
         P.G = t.G;
@@ -1181,7 +1280,6 @@ kn_status noalloc_prepare(kn_network* n, const kn_opts* o, int32_t n_zones, cons
     Pd.N = n->N;
     Pd.R = n->R;
     Pd.S_r = n->S_r;
-    Pd.n_fix = tb.n_fix;
     Pd.zero_idx = n->R + n->S_r;
     Pd.smem_tables = smem_tables;
     Pd.G = G;

@@ -132,7 +132,6 @@ struct GroupPtrs {
     const uint2* shdr;
     const uint16_t* sdst;
     const uint16_t* sidx;
-    const ushort4* fix;
     unsigned char* gbase;
     void* V;
     void* K;
@@ -586,7 +585,6 @@ __device__ void run_group(const PlanDev& P, const OptsDev& O, const unsigned cha
     g.shdr = (const uint2*)(tb + P.tl.off_shdr);
     g.sdst = (const uint16_t*)(tb + P.tl.off_sdst);
     g.sidx = (const uint16_t*)(tb + P.tl.off_sidx);
-    g.fix = (const ushort4*)(tb + P.tl.off_fix);
     g.gbase = gbase;
     g.V = gbase + P.gl.off_V;
     g.K = gbase + P.gl.off_K;
@@ -605,7 +603,6 @@ __device__ void run_group(const PlanDev& P, const OptsDev& O, const unsigned cha
     g.feat = (float*)(gbase + P.gl.off_feat);
     g.hist = (int*)(g.feat + 384);
 
-    const ushort4* __restrict__ fix = g.fix;
     real* V = (real*)g.V;
     real* K = (real*)g.K;
     double* Y64 = g.Y64;
@@ -722,10 +719,12 @@ __device__ void run_group(const PlanDev& P, const OptsDev& O, const unsigned cha
                     gs.sync();
                 }
                 // (b) sliced gathers: warp w sums its slices, one row piece per
-                //     lane, and stores each piece's sum (FP64 form: FP64 sums;
-                //     mixed form: plain FP32 sums -- every term of a row is
-                //     positive, so a piece of at most L terms is within
-                //     (L - 1) 2^-24 of its value, relative)
+                //     lane; the pieces of a split row (consecutive lanes, same
+                //     destination) are added by a segmented reduction into
+                //     the first one.  FP64 form: FP64 sums.  Mixed form: plain
+                //     FP32 sums -- every term of a row is positive, so a row of
+                //     k pieces of at most L terms is within (L - 1 + ceil(log2 k))
+                //     2^-24 of its value, relative.
                 {
                     const int w = lane >> 5, l = lane & 31;
                     const int s1 = g.wsl[w + 1];
@@ -734,34 +733,26 @@ __device__ void run_group(const PlanDev& P, const OptsDev& O, const unsigned cha
                     for (int sl = g.wsl[w]; sl < s1; ++sl) {
                         const uint2 hd = g.shdr[sl];
                         const uint16_t* __restrict__ ix = g.sidx + hd.x + l;
-                        const int len = (int)hd.y;
+                        const int len = (int)(hd.y & 0x7fffffffu);
                         real acc = (real)0;
 #pragma unroll 4
                         for (int k = 0; k < len; ++k) acc = acc + Vr[ix[32 * k]];
-                        *(real*)(Fb + g.sdst[32 * sl + l]) = acc;
+                        const unsigned int d = g.sdst[32 * sl + l];
+                        bool first = true;
+                        if (hd.y >> 31) {  // warp-uniform
+#pragma unroll
+                            for (int off = 1; off < 32; off <<= 1) {
+                                const real o = __shfl_down_sync(0xffffffffu, acc, off);
+                                const unsigned int od = __shfl_down_sync(0xffffffffu, d, off);
+                                if (l + off < 32 && od == d) acc = acc + o;
+                            }
+                            const unsigned int ud = __shfl_up_sync(0xffffffffu, d, 1);
+                            first = l == 0 || ud != d;
+                        }
+                        if (first) *(real*)(Fb + d) = acc;
                     }
                 }
                 gs.sync();
-                // (c) rows split into pieces: the sum of their partials
-                //     (compensated in the mixed form)
-                if (P.n_fix) {
-                    const real* part = (const real*)(gbase + P.gl.off_carry);
-                    unsigned char* __restrict__ Fb = (unsigned char*)Fk;
-                    for (int f = lane; f < P.n_fix; f += G) {
-                        const ushort4 fx = fix[f];
-                        if (PREC == kPrecFP64) {
-                            double sum = 0.0;
-                            for (int p = fx.y; p < fx.y + fx.z; ++p) sum += (double)part[p];
-                            *(real*)(Fb + fx.x) = (real)sum;
-                        } else {
-                            AccKahan ak;
-                            ak.reset();
-                            for (int p = fx.y; p < fx.y + fx.z; ++p) ak.add((float)part[p]);
-                            *(real*)(Fb + fx.x) = (real)__fsub_rn(ak.s, ak.c);
-                        }
-                    }
-                    gs.sync();
-                }
             }
 
             // features of a state reached by an accepted step: training records

@@ -11,14 +11,14 @@ namespace kn {
 // Sci. Comput. 36 (2014), with slices of C = 32 rows, one per warp lane).
 // The 2N row sums -- F+_i (rows 0..N-1: a flux f_j per product slot naming
 // i) and k_i (rows N..2N-1: a reactant-slot partial per slot naming i) --
-// are cut into pieces of at most L terms, sorted by length and packed 32 to
-// a slice.  Slice s has length len_s (its longest piece) and holds lane l's
-// term k at sidx[base_s + 32 k + l] (a V index; shorter pieces are padded
-// with the constant-zero entry).  Warp w of a zone group sums slices
-// wsl[w] .. wsl[w + 1] - 1 and stores lane l's sum at byte offset
-// sdst[32 s + l] from the zone's Fk array: a row slot (0..2N-1), the
-// partial slot fk_span + p of a split row, or the spare slot fk_span + 2G - 1.
-// Split rows are summed from their partials afterwards (fix records).
+// are cut into pieces of at most L terms; a row's pieces occupy consecutive
+// lanes of one slice.  Slice s has length len_s and holds lane l's term k at
+// sidx[base_s + 32 k + l] (a V index; shorter pieces are padded with the
+// constant-zero entry).  Warp w of a zone group sums slices wsl[w] ..
+// wsl[w + 1] - 1; in a slice flagged as holding a split row, a segmented
+// warp reduction adds each row's pieces into its first lane.  Each row's sum
+// is stored at byte offset sdst[32 s + l] from the zone's Fk array (padding
+// lanes store to the spare slot fk_span).
 
 // Fk holds 2N values of `real_bytes` each, padded to 16 bytes; the chunk
 // partials follow directly, so slot fk_span + c addresses them through Fk.
@@ -48,10 +48,9 @@ struct TableLayout {
     int32_t off_cexp;     // real[R]: c_j = n_j + 3 (r_j - 1), so that along the profile
                           //   k_j(t) = k_j(T0, rho0) exp(-c_j t / tau)
     int32_t off_wsl;      // uint16[W + 1]: slice range of each warp (W = G / 32)
-    int32_t off_shdr;     // uint2[n_slices]: (base into sidx, length)
+    int32_t off_shdr;     // uint2[n_slices]: (base into sidx, length | split-row flag << 31)
     int32_t off_sdst;     // uint16[32 n_slices]: destination byte offsets from Fk
     int32_t off_sidx;     // uint16[sum_s 32 len_s]: V indices, lane-interleaved
-    int32_t off_fix;      // ushort4[n_fix]: (row byte offset from Fk, first partial slot, pieces, 0)
 };
 
 // Per-group shared-memory layout (byte offsets inside one group's region).
@@ -64,7 +63,7 @@ struct GroupLayout {
                         //   the low parts of the float-float abundances (0 at entry N)
     int32_t off_Y32;    // float[2][N + 1] (mixed only): the high parts, entry N the constant 1
     int32_t off_Fk;     // real[2N]: F+ then k (mixed: Kahan sums rounded to float)
-    int32_t off_carry;  // chunk partials of rows that cross chunks: real[2][Q] (head, tail)
+    int32_t off_carry;  // real[1]: the spare slot padding lanes of the gather store to
     int32_t off_red;    // per-warp reduction scratch, W = G/32 warps: double[W] x 3, float[W], int[W]
     int32_t off_feat;   // learned proposal / records: float[64 feats, 64 inputs, 128 h1, 128 h2],
                         //   int[3][64] histograms + 4 counters (absent when unused)
@@ -98,7 +97,7 @@ struct PlanDev {
     const unsigned char* blob;  // device
     TableLayout tl;
     const double2* rate0;        // [R] (ln k0_j, n_j), sorted order, global: zone-load rates
-    int32_t N, R, S_r, n_fix;
+    int32_t N, R, S_r;
     int32_t R1, R12;             // reactions [0,R1) 1-body, [R1,R12) 2-body, [R12,R) 3-body
     double cmax;                 // max_j c_j
     int32_t zero_idx;            // V index of the constant zero (= R + S_r)

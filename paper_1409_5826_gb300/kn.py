@@ -18,7 +18,7 @@ HERE = os.path.dirname(os.path.abspath(__file__))
 LIB_PATH = os.path.join(HERE, "libkn.so")
 HEADER = os.path.join(os.path.dirname(HERE), "include", "kn.h")
 
-KN_OK, KN_ERR_INVALID_ARG, KN_ERR_CUDA, KN_ERR_NOMEM, KN_ERR_STATE = range(5)
+KN_OK, KN_ERR_INVALID_ARG, KN_ERR_CUDA, KN_ERR_NOMEM, KN_ERR_STATE, KN_ERR_INTERNAL = range(6)
 ZONE_STATUS = {0: "ok", 1: "step_limit", 2: "dt_underflow", 3: "nonfinite", 4: "max_reject",
                5: "invalid", 6: "pending"}
 PREC_FP64, PREC_MIXED = 0, 1
@@ -83,6 +83,7 @@ def lib():
         "kn_create_network": (I32, [C.POINTER(_Desc), C.POINTER(P)]),
         "kn_destroy_network": (I32, [P]),
         "kn_network_info": (I32, [P, P, P, P, P]),
+        "kn_check_gather_tables": (I32, [C.POINTER(_Desc), I32, I32, P]),
         "kn_set_zone_conditions": (I32, [P, I32, C.POINTER(_Zones), I32, P]),
         "kn_integrate_batch": (I32, [P, I32, C.POINTER(_Opts), P]),
         "kn_get_abundances": (I32, [P, P, P, P, P, P, P, I32, P]),
@@ -177,6 +178,18 @@ def default_opts() -> _Opts:
 
 def _host(a, dtype):
     return np.ascontiguousarray(a, dtype=dtype)
+
+
+def check_gather_tables(net, precision: int, threads_per_zone: int) -> dict:
+    """Build and verify, on the host only, the gather tables the integrator
+    would use for `net` (kn_check_gather_tables); returns their statistics."""
+    keep = [_host(net.A, np.float64), _host(net.reac, np.int32), _host(net.prod, np.int32),
+            _host(net.ln_k0, np.float64), _host(net.t9_exp, np.float64)]
+    d = _Desc(int(net.n_species), int(net.n_reactions), *[a.ctypes.data for a in keep])
+    st = np.zeros(4, np.int32)
+    _check(lib().kn_check_gather_tables(C.byref(d), precision, threads_per_zone, st.ctypes.data))
+    return {"piece_cap": int(st[0]), "slices": int(st[1]), "warp_terms_per_lane": int(st[2]),
+            "table_bytes": int(st[3])}
 
 
 class Network:
