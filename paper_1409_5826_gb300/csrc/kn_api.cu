@@ -224,6 +224,9 @@ static kn_status build_tables_host(const kn_network* n, int prec, int Q, std::ve
     const int fspan = fk_span(N, real_bytes);
     const int G = Q, W = G / 32;
     const int spare = fspan;  // padding lanes store here
+    // Fk holds (F+_i, k_i) pairs: row r < N (F+) at slot 2r, row N + i (k) at 2i + 1
+    auto slot_of = [N](int r) { return r < N ? 2 * r : 2 * (r - N) + 1; };
+    auto row_of = [N](int slot) { return slot % 2 ? N + slot / 2 : slot / 2; };
     if ((spare + 1) * real_bytes > 0xffff) return fail(KN_ERR_INVALID_ARG, "network too large for the gather tables");
     size_t maxlen = 0;
     for (auto& r : rows) maxlen = std::max(maxlen, r.size());
@@ -274,7 +277,7 @@ static kn_status build_tables_host(const kn_network* n, int prec, int Q, std::ve
                 seg |= k > 1;
                 for (int q = 0, st = 0; q < k; ++q) {
                     const int pl = len / k + (q < len % k ? 1 : 0);
-                    sl.push_back({r, st, pl, r * real_bytes});
+                    sl.push_back({r, st, pl, slot_of(r) * real_bytes});
                     st += pl;
                 }
             }
@@ -319,6 +322,10 @@ static kn_status build_tables_host(const kn_network* n, int prec, int Q, std::ve
     if (!L_best) return fail(KN_ERR_INVALID_ARG, "no gather layout fits %d threads per zone", G);
     // flatten: slices in warp order; header (base into sidx, length | split flag << 31)
     std::vector<uint16_t> wsl(W + 1, 0), sdst, sidx;
+    // the terms as byte offsets into V when they fit 16 bits (the loads then
+    // need no scaling), else as indices
+    const bool byte_off = (zero_idx + 1) * real_bytes <= 0x10000;
+    const int vscale = byte_off ? real_bytes : 1;
     std::vector<uint32_t> shdr;
     int n_slices = 0;
     for (int w = 0; w < W; ++w) {
@@ -335,9 +342,9 @@ static kn_status build_tables_host(const kn_network* n, int prec, int Q, std::ve
             shdr.push_back((uint32_t)sidx.size());
             shdr.push_back((uint32_t)len | (best.seg[s] ? 0x80000000u : 0u));
             const size_t base = sidx.size();
-            sidx.resize(base + 32 * (size_t)len, (uint16_t)zero_idx);
+            sidx.resize(base + 32 * (size_t)len, (uint16_t)(zero_idx * vscale));
             for (int l = 0; l < 32; ++l)
-                for (int k = 0; k < len; ++k) sidx[base + 32 * (size_t)k + l] = ordered[l][k];
+                for (int k = 0; k < len; ++k) sidx[base + 32 * (size_t)k + l] = (uint16_t)(ordered[l][k] * vscale);
             ++n_slices;
         }
     }
@@ -357,7 +364,9 @@ static kn_status build_tables_host(const kn_network* n, int prec, int Q, std::ve
                 for (int l = 0; l < 32; ++l) {
                     acc[l] = 0.0;
                     for (uint32_t k = 0; k < len; ++k) {
-                        const uint16_t v = sidx[base + 32 * k + l];
+                        const int raw = sidx[base + 32 * k + l];
+                        if (raw % vscale) return fail(KN_ERR_INTERNAL, "gather table: misaligned value offset");
+                        const int v = raw / vscale;
                         if (v > zero_idx) return fail(KN_ERR_INTERNAL, "gather table: value index out of range");
                         acc[l] += v == zero_idx ? 0.0 : (double)v + 1.0;
                     }
@@ -368,7 +377,7 @@ static kn_status build_tables_host(const kn_network* n, int prec, int Q, std::ve
                     double sum = acc[l];
                     while (e < 32 && sdst[32 * sl + e] == d) sum += acc[e++];
                     if (d % real_bytes || d / real_bytes > spare) return fail(KN_ERR_INTERNAL, "gather table: bad destination");
-                    const int r = d / real_bytes;
+                    const int r = d / real_bytes < 2 * N ? row_of(d / real_bytes) : 2 * N;
                     if (r < 2 * N) {
                         if (e - l > 1 && !seg) return fail(KN_ERR_INTERNAL, "gather table: split row in an unflagged slice");
                         if (got[r] >= 0.0) return fail(KN_ERR_INTERNAL, "gather table: row %d stored twice", r);
@@ -389,7 +398,7 @@ static kn_status build_tables_host(const kn_network* n, int prec, int Q, std::ve
     tl.off_A = off;
     off = pad16(off + real * N);
     tl.off_rspec = off;
-    off = pad16(off + 8 * R);
+    off = pad16(off + 4 * R);
     tl.off_cexp = off;
     off = pad16(off + real * R);
     tl.off_wsl = off;
@@ -412,12 +421,11 @@ static kn_status build_tables_host(const kn_network* n, int prec, int Q, std::ve
     }
     for (int jn = 0; jn < R; ++jn) {
         const int j = n->perm[jn];
-        uint16_t rs[4];
-        rs[0] = (uint16_t)n->reac[j * 3];
-        rs[1] = (uint16_t)(n->nr[j] >= 2 ? n->reac[j * 3 + 1] : N);
-        rs[2] = (uint16_t)(n->nr[j] >= 3 ? n->reac[j * 3 + 2] : N);
-        rs[3] = 0;
-        memcpy(blob.data() + tl.off_rspec + 8 * jn, rs, 8);
+        const uint32_t ra = (uint32_t)n->reac[j * 3];
+        const uint32_t rb = (uint32_t)(n->nr[j] >= 2 ? n->reac[j * 3 + 1] : N);
+        const uint32_t rc = (uint32_t)(n->nr[j] >= 3 ? n->reac[j * 3 + 2] : N);
+        const uint32_t rs = ra | rb << 10 | rc << 20;
+        memcpy(blob.data() + tl.off_rspec + 4 * jn, &rs, 4);
         const double c = n->tn[j] + 3.0 * (n->nr[j] - 1);
         if (prec == kPrecFP64) {
             memcpy(blob.data() + tl.off_cexp + 8 * jn, &c, 8);
@@ -430,6 +438,7 @@ static kn_status build_tables_host(const kn_network* n, int prec, int Q, std::ve
     memcpy(blob.data() + tl.off_shdr, shdr.data(), 4 * shdr.size());
     memcpy(blob.data() + tl.off_sdst, sdst.data(), 2 * sdst.size());
     memcpy(blob.data() + tl.off_sidx, sidx.data(), 2 * sidx.size());
+    tl.sidx_bytes = byte_off ? 1 : 0;
     T.tl = tl;
     T.L = L_best;
     T.n_slices = n_slices;
@@ -885,7 +894,8 @@ static kn_status validate_opts(const kn_opts* o) {
 // eps_r m.  Outside 8x that band the FP32 compare decides as the FP64 one does.
 static void set_guard_band(OptsDev& D, const kn_opts* o) {
     const double u = 5.9604644775390625e-08;  // 2^-24
-    const double band = 8.0 * (2.0 * u / o->eps_r + 4.0 * u);
+    // the test compares the ratio |d| / m, itself within 2 ulp (__fdividef)
+    const double band = 8.0 * (2.0 * u / o->eps_r + 4.0 * u) + 8.0 * u;
     D.eps_r32 = (float)o->eps_r;
     D.kappa32 = (float)o->kappa;
     D.eps_c32 = (float)o->eps_c;
@@ -894,6 +904,8 @@ static void set_guard_band(OptsDev& D, const kn_opts* o) {
     D.grow32 = (float)o->grow_max;
     D.band_lo32 = (float)(1.0 - band);
     D.band_hi32 = (float)(1.0 + band);
+    D.thr_lo32 = (float)(o->eps_r * (1.0 - band));
+    D.thr_hi32 = (float)(o->eps_r * (1.0 + band));
     D.ymin_lo32 = (float)(o->y_min * (1.0 - 8.0 * u));
     D.ymin_hi32 = (float)(o->y_min * (1.0 + 8.0 * u));
 }

@@ -20,6 +20,7 @@
 #include <cuda_bf16.h>
 
 #include <cstdint>
+#include <type_traits>
 
 #include "kn_internal.h"
 
@@ -126,7 +127,7 @@ __device__ __forceinline__ void leader_prepare(GroupState& S, const PlanDev& P, 
 // ---------------------------------------------------------------------------
 struct GroupPtrs {
     const void* A;  // real[N]
-    const ushort4* rspec;
+    const uint32_t* rspec;  // reactants a | b << 10 | c << 20 (N = none)
     const void* cexp;
     const uint16_t* wsl;
     const uint2* shdr;
@@ -161,7 +162,7 @@ __device__ __forceinline__ void update_reduce_fp64(const PlanDev& P, const OptsD
     const double kappa = O.kappa, ymin = O.y_min;
     double csum = 0.0, bn = 0.0, bd = 1.0;
     for (int i = lane; i < N; i += G) {
-        const double y = Yc[i], fp = Fk[i], kk = Fk[N + i];
+        const double y = Yc[i], fp = Fk[2 * i], kk = Fk[2 * i + 1];
         const double kdt = kk * h;
         const double yn = (kdt >= kappa) ? (y + h * fp) / (1.0 + kdt) : y + h * (fp - kk * y);
         Yn64[i] = yn;
@@ -219,7 +220,7 @@ __device__ __forceinline__ void two_sum(float a, float b, float& s, float& e) {
 __device__ __forceinline__ void update_reduce_mixed(const PlanDev& P, const OptsDev& O, const GroupPtrs& g, int lane,
                                                     int cur, double h, int z) {
     const int N = P.N, G = P.G, NP1 = N + 1;
-    const float* Fk = (const float*)g.Fk;
+    const float2* Fk = (const float2*)g.Fk;  // (F+_i, k_i)
     const float* A = (const float*)g.A;
     const float* Yh = g.Y32 + cur * NP1;
     const float* Yl = g.Ylo + cur * NP1;
@@ -228,8 +229,10 @@ __device__ __forceinline__ void update_reduce_mixed(const PlanDev& P, const Opts
     const float h32 = (float)h;
     float cs_h = 0.f, cs_l = 0.f, rmax = 0.f;
     int ok = 1;
-    for (int i = lane; i < N; i += G) {
-        const float yh = Yh[i], yl = Yl[i], fp = Fk[i], kk = Fk[N + i];
+    // species i; FIRST: the lane's first species starts the sums
+    auto body = [&](int i, auto first) {
+        const float2 fk = Fk[i];
+        const float yh = Yh[i], yl = Yl[i], fp = fk.x, kk = fk.y;
         const float kdt = __fmul_rn(kk, h32);
         float nh, nl, dh, dl;
         if (kdt >= O.kappa32) {
@@ -252,40 +255,47 @@ __device__ __forceinline__ void update_reduce_mixed(const PlanDev& P, const Opts
         const float a = A[i];
         const float p = __fmul_rn(a, dh);
         const float pe = fmaf(a, dh, -p);
-        float s, e;
-        two_sum(cs_h, p, s, e);
-        cs_h = s;
-        cs_l = __fadd_rn(cs_l, __fadd_rn(e, fmaf(a, dl, pe)));
+        if (decltype(first)::value) {
+            cs_h = p;
+            cs_l = fmaf(a, dl, pe);
+        } else {
+            float s, e;
+            two_sum(cs_h, p, s, e);
+            cs_h = s;
+            cs_l = __fadd_rn(cs_l, __fadd_rn(e, fmaf(a, dl, pe)));
+        }
         // The accept test's decisions are those of the compares m > y_min
         // and |d| <= eps_r m on the pairs; they are taken on the high parts
         // when those lie clearly on one side (outside a guard band that
-        // bounds their rounding), and on the pairs in FP64 inside the band.
+        // bounds their rounding and the ratio's division), and on the pairs
+        // in FP64 inside the band.
         const float m32 = fmaxf(yh, nh);
         int tested;
         if (m32 > O.ymin_hi32) tested = 1;
         else if (m32 < O.ymin_lo32) tested = 0;
         else tested = fmax((double)yh + (double)yl, (double)nh + (double)nl) > O.y_min;
         if (tested) {
-            const float d32 = fabsf(__fsub_rn(nh, yh));
-            const float lim = __fmul_rn(O.eps_r32, m32);
+            const float r = __fdividef(fabsf(__fsub_rn(nh, yh)), m32);
             int pass_i;
-            if (d32 < __fmul_rn(lim, O.band_lo32)) {
+            if (r < O.thr_lo32) {
                 pass_i = 1;
-            } else if (d32 > __fmul_rn(lim, O.band_hi32)) {
+            } else if (r > O.thr_hi32) {
                 pass_i = 0;
             } else {
                 const double y = (double)yh + (double)yl, yn = (double)nh + (double)nl;
                 pass_i = fabs(yn - y) <= O.eps_r * (y > yn ? y : yn);
             }
             ok &= pass_i;
-            rmax = fmaxf(rmax, __fdividef(d32, m32));  // the dt proposal, FP32
+            rmax = fmaxf(rmax, r);  // the dt proposal, FP32
         }
         if (O.probe) {
             O.probe_Fp[(size_t)z * N + i] = (double)fp;
             O.probe_k[(size_t)z * N + i] = (double)kk;
             O.probe_Y1[(size_t)z * N + i] = (double)nh + (double)nl;
         }
-    }
+    };
+    if (lane < N) body(lane, std::true_type{});
+    for (int i = lane + G; i < N; i += G) body(i, std::false_type{});
 #pragma unroll
     for (int off = 16; off > 0; off >>= 1) {
         const float oh = __shfl_xor_sync(0xffffffffu, cs_h, off);
@@ -294,13 +304,14 @@ __device__ __forceinline__ void update_reduce_mixed(const PlanDev& P, const Opts
         two_sum(cs_h, oh, s, e);
         cs_h = s;
         cs_l = __fadd_rn(__fadd_rn(cs_l, ol), e);
-        rmax = fmaxf(rmax, __shfl_xor_sync(0xffffffffu, rmax, off));
     }
+    // rmax >= 0, so its bit pattern orders as an unsigned integer
+    const unsigned int rbits = __reduce_max_sync(0xffffffffu, __float_as_uint(rmax));
     ok = __all_sync(0xffffffffu, ok);
     if ((lane & 31) == 0) {
         const int w = lane >> 5;
         ((float2*)g.red_c)[w] = make_float2(cs_h, cs_l);
-        g.red_r[w] = rmax;
+        g.red_r[w] = __uint_as_float(rbits);
         g.red_f[w] = ok;
     }
 }
@@ -389,11 +400,11 @@ __device__ void compute_features(const PlanDev& P, const OptsDev& O, const Group
         int asy = 0;
         if (i < N) {
             const float y32 = PREC == kPrecMixed ? g.Y32[cur * NP1 + i] : (float)g.Y64[cur * NP1 + i];
-            const float fp = (float)Fk[i], kk = (float)Fk[N + i];
+            const float fp = (float)Fk[2 * i], kk = (float)Fk[2 * i + 1];
             atomicAdd(&g.hist[exp_bin(y32)], 1);
             atomicAdd(&g.hist[64 + exp_bin(fp)], 1);
             atomicAdd(&g.hist[128 + exp_bin(__fmul_rn(kk, y32))], 1);
-            asy = (double)Fk[N + i] * hp >= kappa;
+            asy = (double)Fk[2 * i + 1] * hp >= kappa;
         }
         const unsigned int bal = __ballot_sync(0xffffffffu, asy);
         if ((lane & 31) == 0 && bal) atomicAdd(&g.hist[192], __popc(bal));
@@ -476,27 +487,27 @@ __device__ float mlp_forward_group(const OptsDev& O, const GroupPtrs& g, const u
 // goes to V[j] and partial q (the product of k_j and the other reactants'
 // abundances) to plane q at Pq[j], so a warp's stores are contiguous.
 template <bool VAR, int NB>
-__device__ __forceinline__ int flux_class(int j, int j_end, int stride, const ushort4* __restrict__ rspec,
+__device__ __forceinline__ int flux_class(int j, int j_end, int stride, const uint32_t* __restrict__ rspec,
                                           const float* __restrict__ cexp, const float* __restrict__ Kz,
                                           const float* __restrict__ Y, float* __restrict__ V,
                                           float* __restrict__ P0, float* __restrict__ P1, float* __restrict__ P2,
                                           float u) {
 #pragma unroll 1
     for (; j < j_end; j += stride) {
-        const ushort4 rs = rspec[j];
+        const uint32_t rs = rspec[j];
         float k = Kz[j];
         if (VAR) k = __fmul_rn(k, ex2_approx(-__fmul_rn(cexp[j], u)));
-        const float ya = Y[rs.x];
+        const float ya = Y[rs & 1023u];
         if (NB == 1) {
             V[j] = __fmul_rn(k, ya);
             P0[j] = k;
         } else if (NB == 2) {
-            const float yb = Y[rs.y];
+            const float yb = Y[(rs >> 10) & 1023u];
             V[j] = __fmul_rn(__fmul_rn(k, ya), yb);
             P0[j] = __fmul_rn(k, yb);
             P1[j] = __fmul_rn(k, ya);
         } else {
-            const float yb = Y[rs.y], yc = Y[rs.z];
+            const float yb = Y[(rs >> 10) & 1023u], yc = Y[rs >> 20];
             const float ka = __fmul_rn(k, ya);
             V[j] = __fmul_rn(__fmul_rn(ka, yb), yc);
             P0[j] = __fmul_rn(__fmul_rn(k, yb), yc);
@@ -516,7 +527,7 @@ __device__ __forceinline__ void flux_pass(const PlanDev& P, const GroupPtrs& g, 
                                           int constant, double s, float u, int poly) {
     using real = typename PrecTraits<PREC>::real;
     const int N = P.N, R = P.R, R1 = P.R1, R12 = P.R12, NP1 = N + 1;
-    const ushort4* __restrict__ rspec = g.rspec;
+    const uint32_t* __restrict__ rspec = g.rspec;
     const real* __restrict__ cexp = (const real*)g.cexp;
     const real* __restrict__ Kz = (const real*)g.K;
     real* __restrict__ Vw = (real*)g.V;
@@ -525,23 +536,23 @@ __device__ __forceinline__ void flux_pass(const PlanDev& P, const GroupPtrs& g, 
         const double* __restrict__ Yr = g.Y64 + buf * NP1;
 #pragma unroll 2
         for (int j = j0; j < R; j += stride) {
-            const ushort4 rs = rspec[j];
+            const uint32_t rs = rspec[j];
             double k = (double)Kz[j];
             if (poly == 2 || poly == 5)
                 k *= exp_neg_small((double)cexp[j] * s, poly);
             else if (poly == 9)
                 k *= exp(-(double)cexp[j] * s);
-            const double ya = Yr[rs.x];
+            const double ya = Yr[rs & 1023u];
             if (j < R1) {
                 Vw[j] = (real)(k * ya);
                 Vw[R + j] = (real)k;
             } else if (j < R12) {
-                const double yb = Yr[rs.y];
+                const double yb = Yr[(rs >> 10) & 1023u];
                 Vw[j] = (real)(k * ya * yb);
                 Vw[R + j] = (real)(k * yb);
                 Vw[pb1 + j] = (real)(k * ya);
             } else {
-                const double yb = Yr[rs.y], yc = Yr[rs.z];
+                const double yb = Yr[(rs >> 10) & 1023u], yc = Yr[rs >> 20];
                 const double ka = k * ya;
                 Vw[j] = (real)(ka * yb * yc);
                 Vw[R + j] = (real)(k * yb * yc);
@@ -579,7 +590,7 @@ __device__ void run_group(const PlanDev& P, const OptsDev& O, const unsigned cha
 
     GroupPtrs g;
     g.A = tb + P.tl.off_A;
-    g.rspec = (const ushort4*)(tb + P.tl.off_rspec);
+    g.rspec = (const uint32_t*)(tb + P.tl.off_rspec);
     g.cexp = tb + P.tl.off_cexp;
     g.wsl = (const uint16_t*)(tb + P.tl.off_wsl);
     g.shdr = (const uint2*)(tb + P.tl.off_shdr);
@@ -728,6 +739,7 @@ __device__ void run_group(const PlanDev& P, const OptsDev& O, const unsigned cha
                 {
                     const int w = lane >> 5, l = lane & 31;
                     const int s1 = g.wsl[w + 1];
+                    const bool boff = P.tl.sidx_bytes != 0;
                     unsigned char* __restrict__ Fb = (unsigned char*)Fk;
                     const real* __restrict__ Vr = V;
                     for (int sl = g.wsl[w]; sl < s1; ++sl) {
@@ -735,8 +747,14 @@ __device__ void run_group(const PlanDev& P, const OptsDev& O, const unsigned cha
                         const uint16_t* __restrict__ ix = g.sidx + hd.x + l;
                         const int len = (int)(hd.y & 0x7fffffffu);
                         real acc = (real)0;
+                        if (boff) {  // byte offsets into V (uniform per table)
+                            const unsigned char* __restrict__ Vb = (const unsigned char*)Vr;
 #pragma unroll 4
-                        for (int k = 0; k < len; ++k) acc = acc + Vr[ix[32 * k]];
+                            for (int k = 0; k < len; ++k) acc = acc + *(const real*)(Vb + ix[32 * k]);
+                        } else {
+#pragma unroll 4
+                            for (int k = 0; k < len; ++k) acc = acc + Vr[ix[32 * k]];
+                        }
                         const unsigned int d = g.sdst[32 * sl + l];
                         bool first = true;
                         if (hd.y >> 31) {  // warp-uniform

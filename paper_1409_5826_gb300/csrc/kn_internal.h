@@ -13,7 +13,8 @@ namespace kn {
 // i) and k_i (rows N..2N-1: a reactant-slot partial per slot naming i) --
 // are cut into pieces of at most L terms; a row's pieces occupy consecutive
 // lanes of one slice.  Slice s has length len_s and holds lane l's term k at
-// sidx[base_s + 32 k + l] (a V index; shorter pieces are padded with the
+// sidx[base_s + 32 k + l] (the value's byte offset in V when every offset
+// fits 16 bits, else its index; shorter pieces are padded with the
 // constant-zero entry).  Warp w of a zone group sums slices wsl[w] ..
 // wsl[w + 1] - 1; in a slice flagged as holding a split row, a segmented
 // warp reduction adds each row's pieces into its first lane.  Each row's sum
@@ -44,13 +45,15 @@ constexpr int kMlpSmemBytes = (kMlpFeatures * kMlpHidden + kMlpHidden * kMlpHidd
 struct TableLayout {
     int32_t bytes;        // total (multiple of 16)
     int32_t off_A;        // real[N] (mass numbers; integers, exact in FP32)
-    int32_t off_rspec;    // ushort4[R]: reactant species a, b, c (N = none), 0
+    int32_t off_rspec;    // uint32[R]: reactant species a | b << 10 | c << 20 (N = none)
     int32_t off_cexp;     // real[R]: c_j = n_j + 3 (r_j - 1), so that along the profile
                           //   k_j(t) = k_j(T0, rho0) exp(-c_j t / tau)
     int32_t off_wsl;      // uint16[W + 1]: slice range of each warp (W = G / 32)
     int32_t off_shdr;     // uint2[n_slices]: (base into sidx, length | split-row flag << 31)
     int32_t off_sdst;     // uint16[32 n_slices]: destination byte offsets from Fk
-    int32_t off_sidx;     // uint16[sum_s 32 len_s]: V indices, lane-interleaved
+    int32_t off_sidx;     // uint16[sum_s 32 len_s]: terms, lane-interleaved: byte offsets into V
+                          //   when sidx_bytes, else V indices
+    int32_t sidx_bytes;   // 1: sidx holds byte offsets
 };
 
 // Per-group shared-memory layout (byte offsets inside one group's region).
@@ -62,7 +65,7 @@ struct GroupLayout {
     int32_t off_Y;      // FP64: double[2][N + 1], entry N the constant 1; mixed: float[2][N + 1],
                         //   the low parts of the float-float abundances (0 at entry N)
     int32_t off_Y32;    // float[2][N + 1] (mixed only): the high parts, entry N the constant 1
-    int32_t off_Fk;     // real[2N]: F+ then k (mixed: Kahan sums rounded to float)
+    int32_t off_Fk;     // real[N][2]: (F+_i, k_i) pairs
     int32_t off_carry;  // real[1]: the spare slot padding lanes of the gather store to
     int32_t off_red;    // per-warp reduction scratch, W = G/32 warps: double[W] x 3, float[W], int[W]
     int32_t off_feat;   // learned proposal / records: float[64 feats, 64 inputs, 128 h1, 128 h2],
@@ -157,6 +160,7 @@ struct OptsDev {
     // FP32 guard band of the mixed form's accept test (see update_reduce)
     float eps_r32, ymin_lo32, ymin_hi32, band_lo32, band_hi32, kappa32;
     float eps_c32, ga32, gb32, grow32;  // mixed form: eps_c and the growth factor's terms in FP32
+    float thr_lo32, thr_hi32;           // mixed form: eps_r times the guard band's ends
     int learn;   // 1: propose with the network
     int record;  // 1: write (features, label) at every accepted state
     int mlp_smem_off;  // byte offset of the staged network in the CTA's shared memory
