@@ -44,6 +44,9 @@ def _args():
     ap.add_argument("--no-forms", action="store_true", help="skip the FP64 and learned-dt side measurements")
     ap.add_argument("--tpz", type=int, default=0)
     ap.add_argument("--tpc", type=int, default=0)
+    ap.add_argument("--sweep", action="store_true",
+                    help="instead of the batch benchmark: time one integration step of a single network "
+                         "against its size (GPU, CPU oracle, CPU backward Euler) and print that table")
     return ap.parse_args()
 
 
@@ -230,6 +233,37 @@ def cpu_baselines(net, zones):
     return exp, be
 
 
+def size_sweep(args):
+    """The single-network scaling study at constant T9 = 7, rho = 1e8: time per
+    accepted step of one zone on the GPU (fastest one-group tiling), of the FP64
+    oracle on one host core and of dense-LU backward Euler on one host core,
+    plus the GPU batch throughput at each size.  One JSON line."""
+    import oracle
+    from kn_inputs import SWEEP_SIZES, constant_zones, sweep_network
+    from paper_1409_5826_gb300 import build, size_sweep as sw
+    build.build()
+    rows = sw.run(SWEEP_SIZES, steps=2000, batch_zones=4096)
+    for row in rows:
+        net = sweep_network(row["n_species"])
+        orc = oracle.Oracle(net)
+        z = constant_zones(net, 1, T9=sw.T9, rho=sw.RHO, t_end=sw.T_END)
+        t0 = time.perf_counter()
+        r = orc.integrate(z, 0, oracle.OracleOpts(max_steps=2000))
+        el = time.perf_counter() - t0
+        row["cpu_oracle_explicit"] = {"s_per_step": el / max(1, r["steps"]), "steps": int(r["steps"]), "cores": 1}
+        be_steps = 200 if net.n_species <= 64 else (50 if net.n_species <= 150 else 20)
+        t0 = time.perf_counter()
+        b = orc.be_integrate(z, 0, oracle.OracleOpts(max_steps=be_steps), max_iter=6)
+        el = time.perf_counter() - t0
+        row["cpu_backward_euler"] = {"s_per_step": el / max(1, b["steps"]), "steps": int(b["steps"]), "cores": 1,
+                                     "kind": "dense LU, Newton <= 6 iterations"}
+        g = row["gpu_single_zone"]["s_per_step"]
+        row["explicit_cpu_over_gpu"] = row["cpu_oracle_explicit"]["s_per_step"] / g
+        row["be_cpu_over_gpu"] = row["cpu_backward_euler"]["s_per_step"] / g
+    print(json.dumps({"sweep": "time per integration step vs network size, one zone at T9 = 7, rho = 1e8",
+                      "rows": rows}), flush=True)
+
+
 def _timed_form(kn, g, dz, stream, opts, reps=2):
     """One warm-up and `reps` timed batches of a form; returns (ms/batch, stats)."""
     import torch
@@ -317,6 +351,10 @@ def main():
             dist.barrier()
             dist.destroy_process_group()
         return
+    if args.sweep:
+        if rank == 0:
+            size_sweep(args)
+        return
     import torch
     torch.cuda.set_device(local)
     if world > 1:
@@ -342,9 +380,10 @@ def main():
     stream = torch.cuda.current_stream()
     tuned = None
     if not (args.tpz or args.tpc):
-        # the project's autotuner picks the tiling on this batch (untimed set-up)
+        # the project's autotuner picks the tiling on this batch (untimed
+        # set-up; whole-batch trials, since the batch's tail matters here)
         g.set_zones(dz, stream)
-        tuned = kn.autotune([g], kn.Opts(precision=prec), max_steps=300, stream=stream)
+        tuned = kn.autotune([g], kn.Opts(precision=prec), max_steps=0, stream=stream)
     opts = kn.Opts(precision=prec, use_graph=1, threads_per_zone=args.tpz, threads_per_cta=args.tpc)
     flush = torch.empty(256 * 1024 * 1024 // 4, dtype=torch.float32, device=dev)  # > L2 (129 MB)
 

@@ -339,9 +339,15 @@ typedef struct {
  * and learned/plain form (a tiling in opts still overrides it).  Candidates:
  * zone groups from one warp (small networks) or the smallest warp multiple
  * covering the species, up to CTA-per-zone, each with the most groups per CTA
- * that fit in shared memory and with fewer.  Each trial integrates every zone
- * for at most max_steps accepted steps (the zone state is saved before and
- * restored after each trial).  *best receives the winner.  Synchronises
+ * that fit in shared memory and with fewer.  Each candidate runs once for one
+ * step (building its tables), then is timed.  max_steps > 0: two trials, each
+ * integrating the longest predicted zones (the head of the work queue, twelve
+ * per SM) for at most max_steps accepted steps -- the steady state of a long
+ * batch -- and the better one counts.  max_steps == 0: one trial that
+ * integrates the whole batch, which also weighs the tail, where the longest
+ * zone's per-step latency rather than throughput can set the batch time.  The
+ * zone state is saved before and restored after the trials.  *best receives
+ * the winner.  Synchronises
  * `stream`.  Errors: KN_ERR_INVALID_ARG, KN_ERR_STATE (no zones), KN_ERR_NOMEM,
  * KN_ERR_CUDA.
  */

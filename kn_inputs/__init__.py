@@ -4,13 +4,13 @@ The only module that both the CPU oracle and the CUDA path draw from.  It
 holds no integration arithmetic: rates, fluxes, updates and the timestep
 controller live in the library and, separately, in the oracle.
 """
-from .networks import (Network, binding_energies, chain_network, custom_network, general_network,
-                       net150, net365, pair_network, random_tiny_network)
+from .networks import (SWEEP_SIZES, Network, binding_energies, chain_network, custom_network, general_network,
+                       net150, net365, pair_network, random_tiny_network, sweep_network)
 from .rng import SplitMix64
 from .zones import Zones, constant_zones, mixed_assignment, profile_zones, T_START, T_END
 
 __all__ = [
     "Network", "binding_energies", "chain_network", "custom_network", "general_network", "net150", "net365",
-    "pair_network", "random_tiny_network", "SplitMix64", "Zones", "constant_zones",
+    "pair_network", "random_tiny_network", "sweep_network", "SWEEP_SIZES", "SplitMix64", "Zones", "constant_zones",
     "profile_zones", "mixed_assignment", "T_START", "T_END",
 ]

@@ -245,6 +245,35 @@ def net365(seed: int = 0) -> Network:
     return general_network(365, 4400, 100, int(round(400 * 4400 / 1604)), seed, "net365_4400")
 
 
+SWEEP_SIZES = (16, 32, 64, 100, 150, 250, 365)
+
+
+def sweep_network(n_species: int, seed: int = 0) -> Network:
+    """The network of the size sweep with n_species species.
+
+    16 is the 16/48 chain; 150 and 365 are net150 and net365.  Other sizes use
+    general_network with the reaction count interpolated from those two
+    (10.69 reactions per species at 150, 12.05 at 365, linear in N, and 10.69 per
+    species below 150), reverse pairs in the same 400/1604 proportion, and
+    A_max = 56 at 150 and 100 at 365, interpolated, capped at (N - 4)/2 + 4 so
+    every mass number holds at least two species.
+    """
+    if n_species == 16:
+        return chain_network(seed)
+    if n_species == 150:
+        return net150(seed)
+    if n_species == 365:
+        return net365(seed)
+    if n_species < 24:
+        raise ValueError("sweep networks other than the chain need at least 24 species")
+    per = 1604 / 150 if n_species <= 150 else 1604 / 150 + (n_species - 150) * (4400 / 365 - 1604 / 150) / 215
+    n_reac = int(round(n_species * per))
+    a_max = int(round(56 + (n_species - 150) * 44 / 215)) if n_species > 150 else 56
+    a_max = min(a_max, (n_species - 4) // 2 + 4)
+    return general_network(n_species, n_reac, a_max, int(round(400 * n_reac / 1604)), seed,
+                           f"net{n_species}_{n_reac}")
+
+
 def custom_network(A, reactions, ln_k0, t9_exp, init_X=None, name="custom") -> Network:
     """Hand-built network from explicit reactions [(reactants, products), ...]."""
     return Network(

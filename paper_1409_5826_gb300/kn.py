@@ -374,7 +374,8 @@ class MLP:
 
 def autotune(nets, opts: Opts, max_steps: int = 400, stream=None) -> dict:
     """Time candidate tilings on the networks' current zones; the winner
-    becomes their default tiling for this precision and form."""
+    becomes their default tiling for this precision and form.  max_steps = 0
+    times whole-batch trials (kn_autotune)."""
     arr = (C.c_void_p * len(nets))(*[n.h for n in nets])
     t = _Tiling()
     _check(lib().kn_autotune(arr, len(nets), C.byref(opts.c()), int(max_steps), C.c_void_p(_stream_ptr(stream)),

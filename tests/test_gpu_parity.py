@@ -386,6 +386,25 @@ def test_autotune_picks_a_tiling_and_results_are_unchanged(kn):
         assert np.max(np.abs(r["Y"][i][m] - ref["Y"][i][m]) / ref["Y"][i][m]) < 0.5
 
 
+def test_autotune_whole_batch_trials(kn):
+    # max_steps = 0: every candidate integrates the whole batch; the state is
+    # restored afterwards, so the tuned launch integrates from the start
+    net = net150()
+    z = profile_zones(net, 400, t_end=2e-11)
+    g = kn.Network(net)
+    g.set_zones(z)
+    t = kn.autotune([g], kn.Opts(precision=MIXED), max_steps=0)
+    assert t["candidates"] >= 4 and t["zone_steps_per_s"] > 0
+    kn.integrate_batch([g], kn.Opts(precision=MIXED))
+    r = g.get()
+    assert (r["status"] == 0).all() and np.array_equal(r["t"], z.t_end)
+    g.set_zones(z)
+    kn.integrate_batch([g], kn.Opts(precision=MIXED, threads_per_zone=160, threads_per_cta=160))
+    ref = g.get()
+    # the same zones to within the gather's summation order
+    assert abs(int(r["steps"].sum()) - int(ref["steps"].sum())) <= 0.02 * int(ref["steps"].sum())
+
+
 def test_mixed_sizes_autotuned(kn):
     nets = [chain_network(), net150(), net365()]
     gs = [kn.Network(n) for n in nets]
