@@ -15,7 +15,7 @@ ROOT = os.path.dirname(HERE)
 CSRC = os.path.join(HERE, "csrc")
 BUILD = os.path.join(HERE, "_build")
 LIB = os.path.join(HERE, "libkn.so")
-SOURCES = ["kn_api.cu", "kn_integrate.cu", "kn_noalloc.cu", "kn_mlp.cu"]
+SOURCES = ["kn_api.cu", "kn_tables.cu", "kn_integrate.cu", "kn_noalloc.cu", "kn_mlp.cu"]
 HEADERS = ["kn_internal.h"]
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 NVCC_FLAGS = ["-O3", "-lineinfo", "-std=c++17", "-Xcompiler", "-fPIC", "-Xcompiler", "-O2",
