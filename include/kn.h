@@ -58,12 +58,15 @@ typedef enum { KN_MEM_HOST = 0, KN_MEM_DEVICE = 1 } kn_mem;
 
 typedef enum {
     KN_PREC_FP64 = 0, /* every step of the path in FP64 */
-    KN_PREC_MIXED = 1 /* FP32 rates, fluxes and gathers (every row sum of positive
-                         terms within (L + 5) 2^-24 relative, L <= the longest row);
-                         abundances kept as FP32 high/low pairs (~48 bits); the
-                         kappa-switched update in FP32; the conservation sum as a
-                         float-float sum of exact products; the relative-error
-                         test in FP32 outside a guard band, FP64 inside it */
+    KN_PREC_MIXED = 1, /* FP32 rates, fluxes and gathers (every row sum of positive
+                          terms within (L + 5) 2^-24 relative, L <= the longest row);
+                          abundances kept as FP32 high/low pairs (~48 bits); the
+                          kappa-switched update in FP32; the conservation sum as a
+                          float-float sum of exact products; the relative-error
+                          test in FP32 outside a guard band, FP64 inside it */
+    KN_PREC_MIXED_FP64 = 2 /* FP32 rates and fluxes, Kahan-compensated FP32 gathers;
+                              the kappa-switched update, the conservation sum and the
+                              error test in FP64 (FP64 abundances) */
 } kn_precision;
 
 /*

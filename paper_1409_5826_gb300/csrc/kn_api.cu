@@ -73,9 +73,9 @@ static GroupLayout group_layout(const kn_network* n, int prec, int G, bool feat)
     g.off_K = off;
     off = pad16(off + real * n->R);
     g.off_Y = off;
-    off = pad16(off + (prec == kPrecFP64 ? 8 : 4) * 2 * (n->N + 1));
+    off = pad16(off + (prec == kPrecMixed ? 4 : 8) * 2 * (n->N + 1));
     g.off_Y32 = off;
-    if (prec == kPrecMixed) off = pad16(off + 4 * 2 * (n->N + 1));
+    if (prec != kPrecFP64) off = pad16(off + 4 * 2 * (n->N + 1));
     g.off_Fk = off;
     off = pad16(off + real * 2 * n->N);
     g.off_carry = off;
@@ -213,7 +213,7 @@ kn_status kn_create_network(const kn_network_desc* d, kn_network** out) {
 kn_status kn_check_gather_tables(const kn_network_desc* d, int32_t precision, int32_t threads_per_zone,
                                  int32_t stats[4]) {
     if (!d || !stats) return fail(KN_ERR_INVALID_ARG, "kn_check_gather_tables: NULL argument");
-    if (precision != KN_PREC_FP64 && precision != KN_PREC_MIXED)
+    if (precision != KN_PREC_FP64 && precision != KN_PREC_MIXED && precision != KN_PREC_MIXED_FP64)
         return fail(KN_ERR_INVALID_ARG, "kn_check_gather_tables: bad precision");
     if (threads_per_zone < 32 || threads_per_zone > 1024 || threads_per_zone % 32)
         return fail(KN_ERR_INVALID_ARG, "kn_check_gather_tables: threads_per_zone must be a multiple of 32 in [32, 1024]");
@@ -339,8 +339,8 @@ namespace {
 
 static kn_status validate_opts(const kn_opts* o) {
     if (!o) return fail(KN_ERR_INVALID_ARG, "NULL opts");
-    if (o->precision != KN_PREC_FP64 && o->precision != KN_PREC_MIXED)
-        return fail(KN_ERR_INVALID_ARG, "opts.precision must be KN_PREC_FP64 or KN_PREC_MIXED");
+    if (o->precision != KN_PREC_FP64 && o->precision != KN_PREC_MIXED && o->precision != KN_PREC_MIXED_FP64)
+        return fail(KN_ERR_INVALID_ARG, "opts.precision must be KN_PREC_FP64, KN_PREC_MIXED or KN_PREC_MIXED_FP64");
     if (!(o->kappa > 0 && o->eps_r > 0 && o->eps_c > 0 && o->y_min >= 0 && o->grow_max >= 1 &&
           o->safety > 0 && o->shrink > 0 && o->shrink < 1 && o->dt_min_frac >= 0 && o->max_steps >= 0 &&
           o->max_reject >= 0))
@@ -436,7 +436,7 @@ static kn_status prepare_launch(kn_network* const* nets, int n_nets, const kn_op
             Tiling best;
             const int g0 = o->threads_per_zone ? o->threads_per_zone : base_group(n);
             const int g1 = o->threads_per_zone ? o->threads_per_zone : 512;
-            const bool small = g0 == 32 || prec == kPrecFP64;
+            const bool small = g0 == 32 || prec != kPrecMixed;
             constexpr int kTargetGroups = 5;
             for (int G = g0; G <= g1; G += 32) {
                 Tables* tb;

@@ -79,6 +79,9 @@ template <> struct PrecTraits<kPrecFP64> {
 template <> struct PrecTraits<kPrecMixed> {
     using real = float;
 };
+template <> struct PrecTraits<kPrecMixed64> {
+    using real = float;
+};
 
 // ---------------------------------------------------------------------------
 // leader-only: set up the next attempt (clipped dt, profile factor at t)
@@ -113,7 +116,7 @@ __device__ __forceinline__ void leader_prepare(GroupState& S, const PlanDev& P, 
         // k_j(t) = K_j exp(-c_j s), s = t / tau: T9 = T0 e^{-s}, rho = rho0 e^{-3s}
         const double s = S.t * S.inv_tau;
         S.s = s;
-        if (PREC == kPrecMixed) {
+        if (PREC != kPrecFP64) {
             S.u = __fmul_rn(__double2float_rn(S.t), S.u_scale);
         } else {
             const double xm = P.cmax * s;
@@ -151,23 +154,30 @@ struct GroupPtrs {
 
 // (d) kappa-switched update (Sec. 3, Eq. 3) with step h from buffer cur into
 // nxt, and each warp's share of the error measures (no barrier inside).
-// FP64 form: every step in FP64, in the order of the definitions.
+// FP64 form (R = double): every step in FP64, in the order of the
+// definitions.  Mixed form with the FP64 update (R = float): F+ and k arrive
+// in FP32 and are widened; the update, the conservation sum and the test run
+// in FP64 exactly as in the FP64 form, and an FP32 copy of y' is kept for the
+// FP32 flux pass.
+template <class R>
 __device__ __forceinline__ void update_reduce_fp64(const PlanDev& P, const OptsDev& O, const GroupPtrs& g, int lane,
                                                    int cur, double h, int z) {
     const int N = P.N, G = P.G, NP1 = N + 1;
-    const double* Fk = (const double*)g.Fk;
-    const double* A = (const double*)g.A;
+    const R* Fk = (const R*)g.Fk;
+    const R* A = (const R*)g.A;
     const double* Yc = g.Y64 + cur * NP1;
     double* Yn64 = g.Y64 + (cur ^ 1) * NP1;
+    [[maybe_unused]] float* Yn32 = g.Y32 + (cur ^ 1) * NP1;
     const double kappa = O.kappa, ymin = O.y_min;
     double csum = 0.0, bn = 0.0, bd = 1.0;
     for (int i = lane; i < N; i += G) {
-        const double y = Yc[i], fp = Fk[2 * i], kk = Fk[2 * i + 1];
+        const double y = Yc[i], fp = (double)Fk[2 * i], kk = (double)Fk[2 * i + 1];
         const double kdt = kk * h;
         const double yn = (kdt >= kappa) ? (y + h * fp) / (1.0 + kdt) : y + h * (fp - kk * y);
         Yn64[i] = yn;
+        if (sizeof(R) == 4) Yn32[i] = (float)yn;
         const double d = yn - y;
-        csum = fma(A[i], d, csum);
+        csum = fma((double)A[i], d, csum);
         if ((y > yn ? y : yn) > ymin) {
             const double m = y > yn ? y : yn;
             const double ad = fabs(d);
@@ -321,8 +331,10 @@ __device__ __forceinline__ void update_reduce(const PlanDev& P, const OptsDev& O
                                               int cur, double h, int z) {
     if (PREC == kPrecMixed)
         update_reduce_mixed(P, O, g, lane, cur, h, z);
+    else if (PREC == kPrecMixed64)
+        update_reduce_fp64<float>(P, O, g, lane, cur, h, z);
     else
-        update_reduce_fp64(P, O, g, lane, cur, h, z);
+        update_reduce_fp64<double>(P, O, g, lane, cur, h, z);
 }
 
 // lane 0, after the barrier that follows update_reduce: combine the warps.
@@ -399,7 +411,7 @@ __device__ void compute_features(const PlanDev& P, const OptsDev& O, const Group
         const int i = i0 + lane;
         int asy = 0;
         if (i < N) {
-            const float y32 = PREC == kPrecMixed ? g.Y32[cur * NP1 + i] : (float)g.Y64[cur * NP1 + i];
+            const float y32 = PREC != kPrecFP64 ? g.Y32[cur * NP1 + i] : (float)g.Y64[cur * NP1 + i];
             const float fp = (float)Fk[2 * i], kk = (float)Fk[2 * i + 1];
             atomicAdd(&g.hist[exp_bin(y32)], 1);
             atomicAdd(&g.hist[64 + exp_bin(fp)], 1);
@@ -646,6 +658,7 @@ __device__ void run_group(const PlanDev& P, const OptsDev& O, const unsigned cha
                     Ylo[i] = __double2float_rn(y - (double)hi);
                 } else {
                     Y64[i] = y;
+                    if (PREC == kPrecMixed64) Y32[i] = (float)y;
                 }
                 bad |= !(isfinite(y) && y >= 0.0);
             }
@@ -658,6 +671,10 @@ __device__ void run_group(const PlanDev& P, const OptsDev& O, const unsigned cha
                 } else {
                     Y64[N] = 1.0;
                     Y64[NP1 + N] = 1.0;
+                    if (PREC == kPrecMixed64) {
+                        Y32[N] = 1.0f;
+                        Y32[NP1 + N] = 1.0f;
+                    }
                 }
                 const double T0 = P.T0[z], rho0 = P.rho0[z], tau = P.tau[z];
                 const double ts = P.t_start[z], te = P.t_end[z], dtt = P.dt_trial[z];
@@ -719,7 +736,7 @@ __device__ void run_group(const PlanDev& P, const OptsDev& O, const unsigned cha
         // have_a: phase (a) of the current state was already computed, by the
         // speculative pass that overlapped the previous decision
         bool have_a = false;
-        const bool spec = G >= 64 && PREC == kPrecMixed;
+        const bool spec = G >= 64 && PREC != kPrecFP64;
         while (!S.done) {
             const int cur = S.cur, nxt = cur ^ 1;
 
@@ -735,7 +752,9 @@ __device__ void run_group(const PlanDev& P, const OptsDev& O, const unsigned cha
                 //     the first one.  FP64 form: FP64 sums.  Mixed form: plain
                 //     FP32 sums -- every term of a row is positive, so a row of
                 //     k pieces of at most L terms is within (L - 1 + ceil(log2 k))
-                //     2^-24 of its value, relative.
+                //     2^-24 of its value, relative.  Mixed form with the FP64
+                //     update: Kahan-compensated FP32 sums, and the pieces'
+                //     (sum, compensation) pairs added with TwoSum.
                 {
                     const int w = lane >> 5, l = lane & 31;
                     const int s1 = g.wsl[w + 1];
@@ -746,6 +765,39 @@ __device__ void run_group(const PlanDev& P, const OptsDev& O, const unsigned cha
                         const uint2 hd = g.shdr[sl];
                         const uint16_t* __restrict__ ix = g.sidx + hd.x + l;
                         const int len = (int)(hd.y & 0x7fffffffu);
+                        const unsigned int d = g.sdst[32 * sl + l];
+                        if (PREC == kPrecMixed64) {
+                            AccKahan ak;
+                            ak.reset();
+                            if (boff) {
+                                const unsigned char* __restrict__ Vb = (const unsigned char*)Vr;
+#pragma unroll 4
+                                for (int k = 0; k < len; ++k) ak.add((float)*(const real*)(Vb + ix[32 * k]));
+                            } else {
+#pragma unroll 4
+                                for (int k = 0; k < len; ++k) ak.add((float)Vr[ix[32 * k]]);
+                            }
+                            float hi = ak.s, lo = -ak.c;
+                            bool first = true;
+                            if (hd.y >> 31) {  // warp-uniform
+#pragma unroll
+                                for (int off = 1; off < 32; off <<= 1) {
+                                    const float oh = __shfl_down_sync(0xffffffffu, hi, off);
+                                    const float ol = __shfl_down_sync(0xffffffffu, lo, off);
+                                    const unsigned int od = __shfl_down_sync(0xffffffffu, d, off);
+                                    if (l + off < 32 && od == d) {
+                                        float s2, e2;
+                                        two_sum(hi, oh, s2, e2);
+                                        hi = s2;
+                                        lo = __fadd_rn(__fadd_rn(lo, ol), e2);
+                                    }
+                                }
+                                const unsigned int ud = __shfl_up_sync(0xffffffffu, d, 1);
+                                first = l == 0 || ud != d;
+                            }
+                            if (first) *(real*)(Fb + d) = (real)__fadd_rn(hi, lo);
+                            continue;
+                        }
                         real acc = (real)0;
                         if (boff) {  // byte offsets into V (uniform per table)
                             const unsigned char* __restrict__ Vb = (const unsigned char*)Vr;
@@ -755,7 +807,6 @@ __device__ void run_group(const PlanDev& P, const OptsDev& O, const unsigned cha
 #pragma unroll 4
                             for (int k = 0; k < len; ++k) acc = acc + Vr[ix[32 * k]];
                         }
-                        const unsigned int d = g.sdst[32 * sl + l];
                         bool first = true;
                         if (hd.y >> 31) {  // warp-uniform
 #pragma unroll
@@ -851,7 +902,7 @@ __device__ void run_group(const PlanDev& P, const OptsDev& O, const unsigned cha
                     S.fresh = 1;
                     if (O.replay_dt) {
                         S.dt = h;
-                    } else if (PREC == kPrecFP64) {
+                    } else if (PREC != kPrecMixed) {
                         // FP64 form: the proposal in FP64 as well
                         const double rel = v.bn / v.bd;
                         double gfac = O.grow_max;
@@ -1002,6 +1053,11 @@ cudaError_t launch_integrator(const LaunchParams& lp, int precision, int grid, i
             integrate_kernel<kPrecFP64, true><<<grid, block, lp.smem_bytes, stream>>>(lp);
         else
             integrate_kernel<kPrecFP64, false><<<grid, block, lp.smem_bytes, stream>>>(lp);
+    } else if (precision == kPrecMixed64) {
+        if (feat)
+            integrate_kernel<kPrecMixed64, true><<<grid, block, lp.smem_bytes, stream>>>(lp);
+        else
+            integrate_kernel<kPrecMixed64, false><<<grid, block, lp.smem_bytes, stream>>>(lp);
     } else {
         if (feat)
             integrate_kernel<kPrecMixed, true><<<grid, block, lp.smem_bytes, stream>>>(lp);
@@ -1012,18 +1068,15 @@ cudaError_t launch_integrator(const LaunchParams& lp, int precision, int grid, i
 }
 
 cudaError_t integrator_set_smem_limit(int bytes) {
-    cudaError_t e = cudaFuncSetAttribute(integrate_kernel<kPrecFP64, false>,
-                                         cudaFuncAttributeMaxDynamicSharedMemorySize, bytes);
-    if (e == cudaSuccess)
-        e = cudaFuncSetAttribute(integrate_kernel<kPrecMixed, false>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                 bytes);
-    if (e == cudaSuccess)
-        e = cudaFuncSetAttribute(integrate_kernel<kPrecFP64, true>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                 bytes);
-    if (e == cudaSuccess)
-        e = cudaFuncSetAttribute(integrate_kernel<kPrecMixed, true>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                 bytes);
-    return e;
+    const void* fns[] = {(const void*)integrate_kernel<kPrecFP64, false>, (const void*)integrate_kernel<kPrecFP64, true>,
+                         (const void*)integrate_kernel<kPrecMixed, false>, (const void*)integrate_kernel<kPrecMixed, true>,
+                         (const void*)integrate_kernel<kPrecMixed64, false>,
+                         (const void*)integrate_kernel<kPrecMixed64, true>};
+    for (const void* f : fns) {
+        const cudaError_t e = cudaFuncSetAttribute(f, cudaFuncAttributeMaxDynamicSharedMemorySize, bytes);
+        if (e != cudaSuccess) return e;
+    }
+    return cudaSuccess;
 }
 
 cudaError_t integrator_occupancy(int precision, int block, int smem, int* blocks_per_sm) {
@@ -1031,6 +1084,9 @@ cudaError_t integrator_occupancy(int precision, int block, int smem, int* blocks
     // by shared memory and block size
     if (precision == kPrecFP64)
         return cudaOccupancyMaxActiveBlocksPerMultiprocessor(blocks_per_sm, integrate_kernel<kPrecFP64, false>,
+                                                             block, smem);
+    if (precision == kPrecMixed64)
+        return cudaOccupancyMaxActiveBlocksPerMultiprocessor(blocks_per_sm, integrate_kernel<kPrecMixed64, false>,
                                                              block, smem);
     return cudaOccupancyMaxActiveBlocksPerMultiprocessor(blocks_per_sm, integrate_kernel<kPrecMixed, false>, block,
                                                          smem);

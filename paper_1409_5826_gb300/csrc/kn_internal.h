@@ -30,6 +30,7 @@ constexpr int kMaxPlans = 4;      // networks per launch
 constexpr int kMaxGroups = 15;    // named barriers 1..15
 constexpr int kPrecFP64 = 0;
 constexpr int kPrecMixed = 1;
+constexpr int kPrecMixed64 = 2;  // FP32 rates, fluxes and Kahan gathers; FP64 update, conservation sum and test
 constexpr int kMlpFeatures = 64;   // learned-proposal network: 64 -> 128 -> 128 -> 1
 constexpr int kMlpHidden = 128;
 constexpr int kMlpParams = kMlpFeatures * kMlpHidden + kMlpHidden + kMlpHidden * kMlpHidden + kMlpHidden +
@@ -62,9 +63,10 @@ struct GroupLayout {
     int32_t off_V;      // real[R + S_r + 1]: fluxes f_j, partial planes 0, 1, 2 (reactions with
                         //   more than 0, 1, 2 reactants), constant 0
     int32_t off_K;      // real[R]: the zone's rates at (T0, rho0)
-    int32_t off_Y;      // FP64: double[2][N + 1], entry N the constant 1; mixed: float[2][N + 1],
-                        //   the low parts of the float-float abundances (0 at entry N)
-    int32_t off_Y32;    // float[2][N + 1] (mixed only): the high parts, entry N the constant 1
+    int32_t off_Y;      // FP64 and mixed-FP64: double[2][N + 1], entry N the constant 1; mixed:
+                        //   float[2][N + 1], the low parts of the float-float abundances (0 at N)
+    int32_t off_Y32;    // float[2][N + 1] (FP32-flux forms): the FP32 copy the flux pass reads (the
+                        //   high parts in the mixed form), entry N the constant 1
     int32_t off_Fk;     // real[N][2]: (F+_i, k_i) pairs
     int32_t off_carry;  // real[1]: the spare slot padding lanes of the gather store to
     int32_t off_red;    // per-warp reduction scratch, W = G/32 warps: double[W] x 3, float[W], int[W]

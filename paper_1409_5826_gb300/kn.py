@@ -21,7 +21,7 @@ HEADER = os.path.join(os.path.dirname(HERE), "include", "kn.h")
 KN_OK, KN_ERR_INVALID_ARG, KN_ERR_CUDA, KN_ERR_NOMEM, KN_ERR_STATE, KN_ERR_INTERNAL = range(6)
 ZONE_STATUS = {0: "ok", 1: "step_limit", 2: "dt_underflow", 3: "nonfinite", 4: "max_reject",
                5: "invalid", 6: "pending"}
-PREC_FP64, PREC_MIXED = 0, 1
+PREC_FP64, PREC_MIXED, PREC_MIXED_FP64 = 0, 1, 2
 MEM_HOST, MEM_DEVICE = 0, 1
 
 

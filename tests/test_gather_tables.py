@@ -26,7 +26,7 @@ def kn():
 def test_benchmark_networks(kn, which):
     net = {"chain": chain_network, "net150": net150, "net365": net365}[which]()
     terms = sum(net.slot_counts())
-    for prec in (kn.PREC_MIXED, kn.PREC_FP64):
+    for prec in (kn.PREC_MIXED, kn.PREC_FP64, kn.PREC_MIXED_FP64):
         for G in (32, 64, 128, 160, 192, 256, 384, 512, 1024):
             st = kn.check_gather_tables(net, prec, G)
             # the longest warp sums at least its share of the terms
@@ -37,14 +37,14 @@ def test_benchmark_networks(kn, which):
 def test_random_networks(kn):
     for seed in range(60):
         net = random_tiny_network(3 + seed % 20, 2 + (7 * seed) % 40, seed)
-        for prec in (kn.PREC_MIXED, kn.PREC_FP64):
+        for prec in (kn.PREC_MIXED, kn.PREC_FP64, kn.PREC_MIXED_FP64):
             for G in (32, 64, 96):
                 kn.check_gather_tables(net, prec, G)
 
 
 def test_bad_arguments(kn):
     net = chain_network()
-    for prec, G in ((2, 64), (kn.PREC_MIXED, 48), (kn.PREC_MIXED, 0), (kn.PREC_MIXED, 2048)):
+    for prec, G in ((3, 64), (kn.PREC_MIXED, 48), (kn.PREC_MIXED, 0), (kn.PREC_MIXED, 2048)):
         with pytest.raises(kn.KnError) as e:
             kn.check_gather_tables(net, prec, G)
         assert e.value.code == kn.KN_ERR_INVALID_ARG

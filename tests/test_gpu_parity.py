@@ -9,12 +9,14 @@ Tiers:
      step counts and statuses.
 Tolerances (relative, on the abundances the accept test looks at, Y > 1e-10):
   FP64 path:  1e-12 one step; 1e-9 replayed (the FP64 bar); free-running 10*eps_r.
-  Mixed path: 1e-5 one step; 1e-4 replayed; free-running 10*eps_r.
+  Mixed paths (float-float state, or FP64 update): 1e-5 one step; 1e-4
+  replayed; free-running 10*eps_r.
 The FP64 one-step bound comes from rounding: the oracle evaluates
 k0 T9^n rho^(r-1) with pow and sums without FMA, the GPU evaluates
 exp(ln k0 + n ln T9 + (r-1) ln rho) with FMA, a few ulp apart per term.
 The mixed bound comes from FP32 rates/fluxes (~4 ulp = 5e-7 per flux) and
-Kahan-compensated FP32 gathers.
+FP32 gathers (plain within a row piece, Kahan-compensated in the FP64-update
+form).
 """
 import math
 
@@ -26,9 +28,9 @@ from kn_inputs import (Zones, chain_network, constant_zones, custom_network, net
 
 pytestmark = pytest.mark.gpu
 
-FP64, MIXED = 0, 1
-TOL_STEP = {FP64: 1e-12, MIXED: 1e-5}  # Y' on the scale max(Y, Y')
-TOL_REPLAY = {FP64: 1e-9, MIXED: 1e-4}
+FP64, MIXED, M64 = 0, 1, 2  # M64: FP32 fluxes and Kahan gathers, FP64 update and test
+TOL_STEP = {FP64: 1e-12, MIXED: 1e-5, M64: 1e-5}  # Y' on the scale max(Y, Y')
+TOL_REPLAY = {FP64: 1e-9, MIXED: 1e-4, M64: 1e-4}
 
 
 @pytest.fixture(scope="module")
@@ -70,7 +72,7 @@ def _zones_with(net, Y, T0, rho0, tau, t_start, dt):
 TILINGS = [(0, 0), (32, 32), (64, 128), (128, 256), (256, 256)]
 
 
-@pytest.mark.parametrize("prec", [FP64, MIXED])
+@pytest.mark.parametrize("prec", [FP64, MIXED, M64])
 @pytest.mark.parametrize("factory", [chain_network, net150, net365])
 @pytest.mark.parametrize("tiling", TILINGS)
 def test_one_step_parity(kn, oracle_mod, prec, factory, tiling):
@@ -138,7 +140,7 @@ def _replay(kn, net, zones, dts_list, prec, tiling=(0, 0)):
     return r
 
 
-@pytest.mark.parametrize("prec", [FP64, MIXED])
+@pytest.mark.parametrize("prec", [FP64, MIXED, M64])
 def test_replay_parity_150(kn, oracle_mod, prec):
     net = net150()
     orc = oracle_mod.Oracle(net)
@@ -152,7 +154,7 @@ def test_replay_parity_150(kn, oracle_mod, prec):
         assert err < TOL_REPLAY[prec], (i, err)
 
 
-@pytest.mark.parametrize("prec", [FP64, MIXED])
+@pytest.mark.parametrize("prec", [FP64, MIXED, M64])
 def test_replay_parity_chain_full_interval(kn, oracle_mod, prec):
     net = chain_network()
     orc = oracle_mod.Oracle(net)
@@ -163,7 +165,7 @@ def test_replay_parity_chain_full_interval(kn, oracle_mod, prec):
     assert _rel_err(r["Y"][0], rec["Y"], 1e-10) < TOL_REPLAY[prec]
 
 
-@pytest.mark.parametrize("prec", [FP64, MIXED])
+@pytest.mark.parametrize("prec", [FP64, MIXED, M64])
 def test_replay_parity_365(kn, oracle_mod, prec):
     net = net365()
     orc = oracle_mod.Oracle(net)
@@ -177,7 +179,7 @@ def test_replay_parity_365(kn, oracle_mod, prec):
 # --------------------------------------------------------------------------
 # tier 3: free-running controller
 # --------------------------------------------------------------------------
-@pytest.mark.parametrize("prec", [FP64, MIXED])
+@pytest.mark.parametrize("prec", [FP64, MIXED, M64])
 def test_free_running_150(kn, oracle_mod, prec):
     net = net150()
     orc = oracle_mod.Oracle(net)
@@ -319,7 +321,7 @@ def test_degenerate_networks(kn, oracle_mod):
               t_start=np.array([1e-3]), t_end=np.array([1.0]), dt_trial=np.array([1e-3]))
     orc = oracle_mod.Oracle(net)
     ref = orc.integrate(z, 0, record=10 ** 6)
-    for prec in (FP64, MIXED):
+    for prec in (FP64, MIXED, M64):
         r = _replay(kn, net, z, [ref["dts"]], prec)
         assert r["Y"][0, 1] == 0.2  # untouched species
         assert _rel_err(r["Y"][0], ref["Y"], 1e-10) < TOL_REPLAY[prec]
@@ -336,7 +338,7 @@ def test_degenerate_networks(kn, oracle_mod):
 # full size: the benchmark's 4096-zone 150/1604 batch in its launch
 # configuration, checked on sampled zones and by properties of every zone
 # --------------------------------------------------------------------------
-@pytest.mark.parametrize("prec", [MIXED, FP64])
+@pytest.mark.parametrize("prec", [MIXED, FP64, M64])
 def test_full_size_batch_sampled(kn, oracle_mod, prec):
     net = net150()
     Z = 4096
@@ -427,7 +429,7 @@ def test_fp64_peak_is_measured(kn):
 # --------------------------------------------------------------------------
 # operator splitting and energy release (Sec. 4, Sec. 6)
 # --------------------------------------------------------------------------
-@pytest.mark.parametrize("prec", [FP64, MIXED])
+@pytest.mark.parametrize("prec", [FP64, MIXED, M64])
 def test_operator_split_chain_and_energy(kn, oracle_mod, prec):
     from kn_inputs import Zones, binding_energies
     from paper_1409_5826_gb300 import opsplit
