@@ -8,13 +8,13 @@
 //   * every group pulls zones from its network's work queue (one atomic per
 //     zone, longest predicted zones first) and keeps the zone resident in
 //     shared memory for its whole integration;
-//   * a network's tables (reactant lists, rate parameters, the flat gather
+//   * a network's tables (reactant lists, rate parameters, the sliced gather
 //     list) are staged once per CTA into shared memory and shared by all
 //     groups;
 //   * per step: rates + fluxes + reactant-slot partials (one pass over
 //     reactions), sliced gathers of F+ and k (each lane sums one row piece
-//     per slice with no per-term branch; long rows are split and their
-//     partials summed afterwards), then the kappa-switched update with
+//     per slice with no per-term branch; a long row's pieces are combined
+//     by a segmented warp reduction), then the kappa-switched update with
 //     deterministic group reductions for the accept test.
 //   * no spin-waits: every loop is bounded by the zone's step and reject limits.
 #include <cuda_bf16.h>
@@ -60,7 +60,7 @@ __device__ __forceinline__ double exp_neg_small(double x, int degree) {
     return fma(x, p, 1.0);
 }
 
-// Kahan-compensated FP32 sum (combines the chunk partials of long rows).
+// Kahan-compensated FP32 sum (the gathers of the mixed form with the FP64 update).
 struct AccKahan {
     float s, c;  // sum and (negated) lost low part: value = s - c
     __device__ __forceinline__ void reset() { s = 0.f; c = 0.f; }

@@ -21,8 +21,8 @@ namespace kn {
 // is stored at byte offset sdst[32 s + l] from the zone's Fk array (padding
 // lanes store to the spare slot fk_span).
 
-// Fk holds 2N values of `real_bytes` each, padded to 16 bytes; the chunk
-// partials follow directly, so slot fk_span + c addresses them through Fk.
+// Fk holds 2N values of `real_bytes` each, padded to 16 bytes; the spare slot
+// that padding lanes of the gather store to follows directly, at slot fk_span.
 constexpr int fk_span(int N, int real_bytes) { return ((real_bytes * 2 * N + 15) & ~15) / real_bytes; }
 
 constexpr int kMaxSpecies = 1023;
@@ -39,8 +39,8 @@ constexpr int kMlpParams = kMlpFeatures * kMlpHidden + kMlpHidden + kMlpHidden *
 constexpr int kMlpSmemBytes = (kMlpFeatures * kMlpHidden + kMlpHidden * kMlpHidden) * 2 +
                               (3 * kMlpHidden + 4 + 2 * kMlpFeatures) * 4;
 
-// One network's tables, as one contiguous device blob per (precision, chunk
-// count); the kernel stages the blob into shared memory when it fits.
+// One network's tables, as one contiguous device blob per (precision, zone
+// group size); the kernel stages the blob into shared memory when it fits.
 // Reactions are stored sorted by reactant count (1-body, 2-body, 3-body) so
 // that the flux loop is warp-uniform and multiplies by no sentinel.
 struct TableLayout {
