@@ -12,7 +12,7 @@ the others), in both precisions.
 import numpy as np
 import pytest
 
-from kn_inputs import chain_network, net150, net365, random_tiny_network
+from kn_inputs import SWEEP_SIZES, chain_network, net150, net365, random_tiny_network, sweep_network
 
 
 @pytest.fixture(scope="module")
@@ -32,6 +32,14 @@ def test_benchmark_networks(kn, which):
             # the longest warp sums at least its share of the terms
             assert st["warp_terms_per_lane"] * 32 * (G // 32) >= terms
             assert st["piece_cap"] >= 1 and st["slices"] >= 1
+
+
+@pytest.mark.parametrize("n", SWEEP_SIZES)
+def test_sweep_networks(kn, n):
+    net = sweep_network(n)
+    for prec in (kn.PREC_MIXED, kn.PREC_FP64):
+        for G in (64, 128, 256, 512):
+            kn.check_gather_tables(net, prec, G)
 
 
 def test_random_networks(kn):
