@@ -72,6 +72,8 @@ static GroupLayout group_layout(const kn_network* n, int prec, int G, bool feat)
     off = pad16(off + real * (n->R + n->S_r + 1));
     g.off_K = off;
     off = pad16(off + real * n->R);
+    g.off_Kc = off;
+    if (prec != kPrecFP64) off = pad16(off + 4 * n->R);
     g.off_Y = off;
     off = pad16(off + (prec == kPrecMixed ? 4 : 8) * 2 * (n->N + 1));
     g.off_Y32 = off;
@@ -337,6 +339,13 @@ kn_status kn_set_zone_conditions(kn_network* n, int32_t Z, const kn_zone_conditi
 
 namespace {
 
+// The FP32-flux forms reuse a zone's cached rates K_j 2^(-c_j u_ref) while
+// |u - u_ref| <= tol: then every rate differs from K_j 2^(-c_j u) by less
+// than c_max ln 2 tol = 2^-26 relative, a quarter of an FP32 ulp.
+static float rate_cache_tol(double cmax) {
+    return cmax > 0.0 ? (float)(1.4901161193847656e-08 / (cmax * 0.6931471805599453)) : 3.0e38f;
+}
+
 static kn_status validate_opts(const kn_opts* o) {
     if (!o) return fail(KN_ERR_INVALID_ARG, "NULL opts");
     if (o->precision != KN_PREC_FP64 && o->precision != KN_PREC_MIXED && o->precision != KN_PREC_MIXED_FP64)
@@ -490,6 +499,7 @@ static kn_status prepare_launch(kn_network* const* nets, int n_nets, const kn_op
         P.R1 = n->R1;
         P.R12 = n->R12;
         P.cmax = n->cmax;
+        P.u_tol = rate_cache_tol(n->cmax);
         P.N = n->N;
         P.R = n->R;
         P.S_r = n->S_r;
@@ -762,6 +772,7 @@ kn_status noalloc_prepare(kn_network* n, const kn_opts* o, int32_t n_zones, cons
     Pd.R1 = n->R1;
     Pd.R12 = n->R12;
     Pd.cmax = n->cmax;
+    Pd.u_tol = rate_cache_tol(n->cmax);
     Pd.N = n->N;
     Pd.R = n->R;
     Pd.S_r = n->S_r;

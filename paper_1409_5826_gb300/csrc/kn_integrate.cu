@@ -139,6 +139,7 @@ struct GroupPtrs {
     unsigned char* gbase;
     void* V;
     void* K;
+    float* Kc;  // FP32-flux forms: the rates at u_ref
     double* Y64;  // FP64 form: the abundances
     float* Ylo;   // mixed form: low parts of the float-float abundances (high parts: Y32)
     float* Y32;
@@ -493,22 +494,29 @@ __device__ float mlp_forward_group(const OptsDev& O, const GroupPtrs& g, const u
     return s + Pb[384];
 }
 
-// Mixed form, one reactant-count class of the sorted reactions: reactions
-// j, j + stride, ... below j_end; returns the first index at or past j_end,
-// where the next class continues.  VAR: k_j(t) = K_j 2^(-c_j u).  The flux
-// goes to V[j] and partial q (the product of k_j and the other reactants'
-// abundances) to plane q at Pq[j], so a warp's stores are contiguous.
-template <bool VAR, int NB>
+// FP32-flux forms, one reactant-count class of the sorted reactions:
+// reactions j, j + stride, ... below j_end; returns the first index at or
+// past j_end, where the next class continues.  The rates come from the
+// group's cache Kc; REFRESH recomputes them first, Kc_j = K_j 2^(-c_j u).
+// The flux goes to V[j] and partial q (the product of k_j and the other
+// reactants' abundances) to plane q at Pq[j], so a warp's stores are
+// contiguous.
+template <bool REFRESH, int NB>
 __device__ __forceinline__ int flux_class(int j, int j_end, int stride, const uint32_t* __restrict__ rspec,
                                           const float* __restrict__ cexp, const float* __restrict__ Kz,
-                                          const float* __restrict__ Y, float* __restrict__ V,
-                                          float* __restrict__ P0, float* __restrict__ P1, float* __restrict__ P2,
-                                          float u) {
+                                          float* __restrict__ Kc, const float* __restrict__ Y,
+                                          float* __restrict__ V, float* __restrict__ P0, float* __restrict__ P1,
+                                          float* __restrict__ P2, float u) {
 #pragma unroll 1
     for (; j < j_end; j += stride) {
         const uint32_t rs = rspec[j];
-        float k = Kz[j];
-        if (VAR) k = __fmul_rn(k, ex2_approx(-__fmul_rn(cexp[j], u)));
+        float k;
+        if (REFRESH) {
+            k = __fmul_rn(Kz[j], ex2_approx(-__fmul_rn(cexp[j], u)));
+            Kc[j] = k;
+        } else {
+            k = Kc[j];
+        }
         const float ya = Y[rs & 1023u];
         if (NB == 1) {
             V[j] = __fmul_rn(k, ya);
@@ -535,8 +543,10 @@ __device__ __forceinline__ int flux_class(int j, int j_end, int stride, const ui
 // 1-, 2-, 3-body, so no multiply by an absent reactant.  s = t / tau (FP64
 // form: poly selects the series for exp(-c_j s)); u = s / ln 2 (mixed form).
 template <int PREC>
+// refresh (FP32-flux forms): recompute the cached rates at u before use; each
+// thread refreshes exactly the reactions it then reads, so no barrier is needed.
 __device__ __forceinline__ void flux_pass(const PlanDev& P, const GroupPtrs& g, int j0, int stride, int buf,
-                                          int constant, double s, float u, int poly) {
+                                          int constant, double s, float u, int poly, bool refresh) {
     using real = typename PrecTraits<PREC>::real;
     const int N = P.N, R = P.R, R1 = P.R1, R12 = P.R12, NP1 = N + 1;
     const uint32_t* __restrict__ rspec = g.rspec;
@@ -577,17 +587,18 @@ __device__ __forceinline__ void flux_pass(const PlanDev& P, const GroupPtrs& g, 
         const float* __restrict__ cf = (const float*)g.cexp;
         const float* __restrict__ Kf = (const float*)g.K;
         float* __restrict__ Vf = (float*)g.V;
+        float* __restrict__ Kc = g.Kc;
         float* P0 = Vf + R;
         float* P1 = Vf + pb1;
         float* P2 = Vf + pb2;
-        if (constant) {
-            int j = flux_class<false, 1>(j0, R1, stride, rspec, cf, Kf, Yc32, Vf, P0, P1, P2, u);
-            j = flux_class<false, 2>(j, R12, stride, rspec, cf, Kf, Yc32, Vf, P0, P1, P2, u);
-            flux_class<false, 3>(j, R, stride, rspec, cf, Kf, Yc32, Vf, P0, P1, P2, u);
+        if (refresh) {
+            int j = flux_class<true, 1>(j0, R1, stride, rspec, cf, Kf, Kc, Yc32, Vf, P0, P1, P2, u);
+            j = flux_class<true, 2>(j, R12, stride, rspec, cf, Kf, Kc, Yc32, Vf, P0, P1, P2, u);
+            flux_class<true, 3>(j, R, stride, rspec, cf, Kf, Kc, Yc32, Vf, P0, P1, P2, u);
         } else {
-            int j = flux_class<true, 1>(j0, R1, stride, rspec, cf, Kf, Yc32, Vf, P0, P1, P2, u);
-            j = flux_class<true, 2>(j, R12, stride, rspec, cf, Kf, Yc32, Vf, P0, P1, P2, u);
-            flux_class<true, 3>(j, R, stride, rspec, cf, Kf, Yc32, Vf, P0, P1, P2, u);
+            int j = flux_class<false, 1>(j0, R1, stride, rspec, cf, Kf, Kc, Yc32, Vf, P0, P1, P2, u);
+            j = flux_class<false, 2>(j, R12, stride, rspec, cf, Kf, Kc, Yc32, Vf, P0, P1, P2, u);
+            flux_class<false, 3>(j, R, stride, rspec, cf, Kf, Kc, Yc32, Vf, P0, P1, P2, u);
         }
     }
 }
@@ -611,6 +622,7 @@ __device__ void run_group(const PlanDev& P, const OptsDev& O, const unsigned cha
     g.gbase = gbase;
     g.V = gbase + P.gl.off_V;
     g.K = gbase + P.gl.off_K;
+    g.Kc = (float*)(gbase + P.gl.off_Kc);
     g.Y64 = (double*)(gbase + P.gl.off_Y);
     g.Ylo = (float*)(gbase + P.gl.off_Y);
     g.Y32 = (float*)(gbase + P.gl.off_Y32);
@@ -690,6 +702,7 @@ __device__ void run_group(const PlanDev& P, const OptsDev& O, const unsigned cha
                 S.s = 0.0;
                 S.poly = 0;
                 S.u = 0.f;
+                S.u_ref = -1e30f;  // the first flux pass computes the cached rates
                 S.steps = 0;
                 S.rejects = 0;
                 S.props = 0;
@@ -743,8 +756,13 @@ __device__ void run_group(const PlanDev& P, const OptsDev& O, const unsigned cha
             if (!S.rhs_valid) {
                 if (!have_a) {
                     // (a) rates, fluxes and reactant-slot partials at this state
-                    flux_pass<PREC>(P, g, lane, G, cur, S.constant, S.s, S.u, S.poly);
+                    // FP32-flux forms: refresh the cached rates when u has moved
+                    // by more than u_tol since they were computed (a rate change
+                    // below a quarter ulp), or at the zone's first pass
+                    const bool refresh = PREC != kPrecFP64 && !(fabsf(S.u - S.u_ref) <= P.u_tol);
+                    flux_pass<PREC>(P, g, lane, G, cur, S.constant, S.s, S.u, S.poly, refresh);
                     gs.sync();
+                    if (lane == 0 && refresh) S.u_ref = S.u;
                 }
                 // (b) sliced gathers: warp w sums its slices, one row piece per
                 //     lane; the pieces of a split row (consecutive lanes, same
@@ -877,13 +895,15 @@ __device__ void run_group(const PlanDev& P, const OptsDev& O, const unsigned cha
             if (spec && lane == 32) {
                 // the candidate state's profile factor (t + h) / (tau ln 2), once per group
                 S.u_spec = S.constant ? 0.f : __fmul_rn(__double2float_rn(S.t + h_now), S.u_scale);
+                S.refresh_spec = !(fabsf(S.u_spec - S.u_ref) <= P.u_tol);
             }
             update_reduce<PREC>(P, O, g, lane, cur, h_now, z);
             gs.sync();
             if (spec && lane >= 32)
-                flux_pass<PREC>(P, g, lane - 32, G - 32, nxt, S.constant, 0.0, S.u_spec, 0);
+                flux_pass<PREC>(P, g, lane - 32, G - 32, nxt, S.constant, 0.0, S.u_spec, 0, S.refresh_spec != 0);
             have_a = spec;
             if (lane == 0) {
+                if (spec && S.refresh_spec) S.u_ref = S.u_spec;  // the speculative pass refreshed Kc
                 const Verdict v = combine<PREC>(P, O, g);
                 const double h = S.h;
                 if (O.probe) {

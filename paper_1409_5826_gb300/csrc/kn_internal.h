@@ -63,6 +63,7 @@ struct GroupLayout {
     int32_t off_V;      // real[R + S_r + 1]: fluxes f_j, partial planes 0, 1, 2 (reactions with
                         //   more than 0, 1, 2 reactants), constant 0
     int32_t off_K;      // real[R]: the zone's rates at (T0, rho0)
+    int32_t off_Kc;     // float[R] (FP32-flux forms): the rates at u_ref, K_j 2^(-c_j u_ref)
     int32_t off_Y;      // FP64 and mixed-FP64: double[2][N + 1], entry N the constant 1; mixed:
                         //   float[2][N + 1], the low parts of the float-float abundances (0 at N)
     int32_t off_Y32;    // float[2][N + 1] (FP32-flux forms): the FP32 copy the flux pass reads (the
@@ -93,8 +94,10 @@ struct GroupState {
     int fresh;         // current state was reached by an accepted step: features due
     int mlp_try;       // the current attempt uses the learned proposal
     int found;         // label search: a grid step passed
-    float u_spec;      // mixed form: (t + h)/(tau ln 2) of the candidate state
-    float u_scale;     // mixed form: 1/(tau ln 2)
+    float u_spec;      // FP32-flux forms: (t + h)/(tau ln 2) of the candidate state
+    float u_scale;     // FP32-flux forms: 1/(tau ln 2)
+    float u_ref;       // FP32-flux forms: the u at which the cached rates Kc were computed
+    int refresh_spec;  // the speculative flux pass recomputes Kc
 };
 
 struct PlanDev {
@@ -105,6 +108,8 @@ struct PlanDev {
     int32_t N, R, S_r;
     int32_t R1, R12;             // reactions [0,R1) 1-body, [R1,R12) 2-body, [R12,R) 3-body
     double cmax;                 // max_j c_j
+    float u_tol;                 // FP32-flux forms: cached rates are reused while |u - u_ref| <= u_tol,
+                                 //   i.e. while no rate would move by a quarter ulp: 2^-26 / (cmax ln 2)
     int32_t zero_idx;            // V index of the constant zero (= R + S_r)
     int32_t smem_tables;         // 1: stage blob into shared memory
     int32_t G, M;                // threads per zone group, groups per CTA
