@@ -134,12 +134,22 @@ def algorithmic_flops(net, steps, rejects):
     return float(steps * (5 * R + per_rx + s_r + s_p) + (steps + rejects) * 11 * net.n_species)
 
 
-def algorithmic_smem_bytes(net, steps, rejects):
-    """Algorithmic shared-memory bytes of the mixed form per batch: each value
-    the method reads or writes, once, in the width the mixed form keeps it.
-      flux pass, per accepted step: per reaction the reactant list (8 B), rate
-        K_j (4 B), exponent c_j (4 B) and flux store (4 B); per reactant slot the
-        abundance read (4 B) and the partial store (4 B):  20 R + 8 S_r
+def algorithmic_smem_bytes(net, steps):
+    """The per-zone-step shared-memory figure of the measurement plan, in the
+    FP32 widths of the mixed form, times the accepted steps of the batch:
+    abundance reads 4 S_r, partial and flux writes 4 (S_r + R), 16-bit gather
+    indices 2 (S_r + S_p) and flux reads of the F+ gathers 4 S_p."""
+    R = net.n_reactions
+    s_r, s_p = net.slot_counts()
+    return float(steps * (4 * s_r + 4 * (s_r + R) + 2 * (s_r + s_p) + 4 * s_p))
+
+
+def full_smem_bytes(net, steps, rejects):
+    """A fuller count, for context: every value the step reads or writes once,
+    in the width the mixed form keeps it.
+      flux pass, per accepted step: per reaction the packed reactant ids (4 B),
+        the cached rate (4 B) and the flux store (4 B); per reactant slot the
+        abundance read (4 B) and the partial store (4 B):  12 R + 8 S_r
       gathers, per accepted step: per term a 16-bit index and a 4 B value, per
         row one 4 B store:  6 (S_r + S_p) + 8 N
       update and test, per attempt: per species the abundance pair, F+, k and
@@ -147,7 +157,7 @@ def algorithmic_smem_bytes(net, steps, rejects):
     R = net.n_reactions
     s_r, s_p = net.slot_counts()
     N = net.n_species
-    return float(steps * (20 * R + 8 * s_r + 6 * (s_r + s_p) + 8 * N) + (steps + rejects) * 28 * N)
+    return float(steps * (12 * R + 8 * s_r + 6 * (s_r + s_p) + 8 * N) + (steps + rejects) * 28 * N)
 
 
 def _profile_line(name):
@@ -477,14 +487,18 @@ def main():
         # SM at the SM clock sampled during the timed steps
         sm_hz = (clk.get("sm_mhz") or 2070.0) * 1e6
         peak = 128.0 * _n_sms() * sm_hz / 1e9
-        b = algorithmic_smem_bytes(net, st["steps"], st["rejects"])
+        b = algorithmic_smem_bytes(net, st["steps"])
+        bf = full_smem_bytes(net, st["steps"], st["rejects"])
         roof = {"bound": "alu", "resource": "shared-memory bandwidth (SM-local)", "unit": "GB/s",
                 "kernel": "integrate_kernel", "achieved": b / (kms / 1e3) / 1e9, "peak": peak,
                 "peak_source": "derived: 128 B/clk/SM x SMs x sampled SM clock",
                 "traffic": traffic,
                 "traffic_source": "profiles/integrate_kernel_mixed_1216x150_full.md, scaled by zones"
                 if traffic else None,
-                "algorithmic_smem_bytes_per_launch": b, "kernel_ms": kms}
+                "algorithmic_smem_bytes_per_launch": b,
+                "algorithmic_unit": "per accepted zone-step: 4 S_r + 4 (S_r + R) + 2 (S_r + S_p) + 4 S_p bytes",
+                "full_count_smem_bytes_per_launch": bf, "full_count_frac": bf / (kms / 1e3) / 1e9 / peak,
+                "kernel_ms": kms}
     else:
         # FP64 pipe bound: the peak is the device's DFMA throughput measured
         # here (the peaks file has no FP64 figure); nominal 1.25 TFLOP/s
