@@ -165,6 +165,20 @@ def test_replay_parity_chain_full_interval(kn, oracle_mod, prec):
     assert _rel_err(r["Y"][0], rec["Y"], 1e-10) < TOL_REPLAY[prec]
 
 
+@pytest.mark.parametrize("prec", [MIXED, M64])
+def test_replay_parity_chain_profiles(kn, oracle_mod, prec):
+    # profiled zones over a long interval: t/tau grows to ~1e-2, so the FP32-flux
+    # forms refresh their cached rates on most steps (and reuse them on the rest)
+    net = chain_network()
+    orc = oracle_mod.Oracle(net)
+    z = profile_zones(net, 6, t_end=1e-3)
+    rec = [orc.integrate(z, i, record=10 ** 6) for i in range(z.n_zones)]
+    r = _replay(kn, net, z, [x["dts"] for x in rec], prec)
+    for i in range(z.n_zones):
+        assert r["steps"][i] == rec[i]["steps"]
+        assert _rel_err(r["Y"][i], rec[i]["Y"], 1e-10) < TOL_REPLAY[prec]
+
+
 @pytest.mark.parametrize("prec", [FP64, MIXED, M64])
 def test_replay_parity_365(kn, oracle_mod, prec):
     net = net365()
