@@ -132,9 +132,13 @@ typedef struct {
     double shrink;         /* default 0.5 */
     double dt_min_frac;    /* default 1e-30 */
     int64_t max_steps;     /* accepted steps per zone, default 10^7 */
-    /* Tiling (0 = autotuned or built-in default): threads per CTA and
-       threads per zone group.  A CTA holds threads_per_cta/threads_per_zone
-       zone slots; threads_per_zone == threads_per_cta is CTA-per-zone. */
+    /* Tiling (0 = the kn_autotune winner if there is one, else the built-in
+       default): threads per CTA and threads per zone group.  A CTA holds
+       threads_per_cta/threads_per_zone zone slots; threads_per_zone ==
+       threads_per_cta is CTA-per-zone.  The built-in default for one network
+       stages the tables in shared memory and takes, in KN_PREC_MIXED with
+       groups of more than one warp, up to 5 groups per CTA and then the largest
+       group; otherwise the most groups per CTA and then the smallest group. */
     int32_t threads_per_cta;
     int32_t threads_per_zone;
     int32_t use_graph;     /* 1: capture the launch sequence in a CUDA graph and replay it */
