@@ -64,6 +64,11 @@ static kn_status get_tables(kn_network* n, int prec, int Q, Tables** out) {
     return KN_OK;
 }
 
+// The FP32-flux forms keep a per-group cache of the current rates (4 R bytes)
+// only for networks of up to 2048 reactions: beyond that the cache would cost
+// a zone group per SM, which is worth more than the saved rate evaluations.
+static bool rate_cache_on(const kn_network* n, int prec) { return prec != kPrecFP64 && 4 * n->R <= 8192; }
+
 static GroupLayout group_layout(const kn_network* n, int prec, int G, bool feat) {
     const int real = prec == kPrecFP64 ? 8 : 4;
     GroupLayout g{};
@@ -73,7 +78,7 @@ static GroupLayout group_layout(const kn_network* n, int prec, int G, bool feat)
     g.off_K = off;
     off = pad16(off + real * n->R);
     g.off_Kc = off;
-    if (prec != kPrecFP64) off = pad16(off + 4 * n->R);
+    if (rate_cache_on(n, prec)) off = pad16(off + 4 * n->R);
     g.off_Y = off;
     off = pad16(off + (prec == kPrecMixed ? 4 : 8) * 2 * (n->N + 1));
     g.off_Y32 = off;
@@ -500,6 +505,7 @@ static kn_status prepare_launch(kn_network* const* nets, int n_nets, const kn_op
         P.R12 = n->R12;
         P.cmax = n->cmax;
         P.u_tol = rate_cache_tol(n->cmax);
+        P.rate_cache = rate_cache_on(n, prec) ? 1 : 0;
         P.N = n->N;
         P.R = n->R;
         P.S_r = n->S_r;
@@ -773,6 +779,7 @@ kn_status noalloc_prepare(kn_network* n, const kn_opts* o, int32_t n_zones, cons
     Pd.R12 = n->R12;
     Pd.cmax = n->cmax;
     Pd.u_tol = rate_cache_tol(n->cmax);
+    Pd.rate_cache = rate_cache_on(n, o->precision) ? 1 : 0;
     Pd.N = n->N;
     Pd.R = n->R;
     Pd.S_r = n->S_r;

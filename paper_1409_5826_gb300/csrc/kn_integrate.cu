@@ -497,7 +497,8 @@ __device__ float mlp_forward_group(const OptsDev& O, const GroupPtrs& g, const u
 // FP32-flux forms, one reactant-count class of the sorted reactions:
 // reactions j, j + stride, ... below j_end; returns the first index at or
 // past j_end, where the next class continues.  The rates come from the
-// group's cache Kc; REFRESH recomputes them first, Kc_j = K_j 2^(-c_j u).
+// group's cache Kc; REFRESH recomputes them, K_j 2^(-c_j u), and stores them
+// to Kc when the plan keeps the cache (`store`).
 // The flux goes to V[j] and partial q (the product of k_j and the other
 // reactants' abundances) to plane q at Pq[j], so a warp's stores are
 // contiguous.
@@ -506,14 +507,14 @@ __device__ __forceinline__ int flux_class(int j, int j_end, int stride, const ui
                                           const float* __restrict__ cexp, const float* __restrict__ Kz,
                                           float* __restrict__ Kc, const float* __restrict__ Y,
                                           float* __restrict__ V, float* __restrict__ P0, float* __restrict__ P1,
-                                          float* __restrict__ P2, float u) {
+                                          float* __restrict__ P2, float u, bool store) {
 #pragma unroll 1
     for (; j < j_end; j += stride) {
         const uint32_t rs = rspec[j];
         float k;
         if (REFRESH) {
             k = __fmul_rn(Kz[j], ex2_approx(-__fmul_rn(cexp[j], u)));
-            Kc[j] = k;
+            if (store) Kc[j] = k;
         } else {
             k = Kc[j];
         }
@@ -592,13 +593,13 @@ __device__ __forceinline__ void flux_pass(const PlanDev& P, const GroupPtrs& g, 
         float* P1 = Vf + pb1;
         float* P2 = Vf + pb2;
         if (refresh) {
-            int j = flux_class<true, 1>(j0, R1, stride, rspec, cf, Kf, Kc, Yc32, Vf, P0, P1, P2, u);
-            j = flux_class<true, 2>(j, R12, stride, rspec, cf, Kf, Kc, Yc32, Vf, P0, P1, P2, u);
-            flux_class<true, 3>(j, R, stride, rspec, cf, Kf, Kc, Yc32, Vf, P0, P1, P2, u);
+            int j = flux_class<true, 1>(j0, R1, stride, rspec, cf, Kf, Kc, Yc32, Vf, P0, P1, P2, u, P.rate_cache != 0);
+            j = flux_class<true, 2>(j, R12, stride, rspec, cf, Kf, Kc, Yc32, Vf, P0, P1, P2, u, P.rate_cache != 0);
+            flux_class<true, 3>(j, R, stride, rspec, cf, Kf, Kc, Yc32, Vf, P0, P1, P2, u, P.rate_cache != 0);
         } else {
-            int j = flux_class<false, 1>(j0, R1, stride, rspec, cf, Kf, Kc, Yc32, Vf, P0, P1, P2, u);
-            j = flux_class<false, 2>(j, R12, stride, rspec, cf, Kf, Kc, Yc32, Vf, P0, P1, P2, u);
-            flux_class<false, 3>(j, R, stride, rspec, cf, Kf, Kc, Yc32, Vf, P0, P1, P2, u);
+            int j = flux_class<false, 1>(j0, R1, stride, rspec, cf, Kf, Kc, Yc32, Vf, P0, P1, P2, u, P.rate_cache != 0);
+            j = flux_class<false, 2>(j, R12, stride, rspec, cf, Kf, Kc, Yc32, Vf, P0, P1, P2, u, P.rate_cache != 0);
+            flux_class<false, 3>(j, R, stride, rspec, cf, Kf, Kc, Yc32, Vf, P0, P1, P2, u, P.rate_cache != 0);
         }
     }
 }
@@ -759,7 +760,7 @@ __device__ void run_group(const PlanDev& P, const OptsDev& O, const unsigned cha
                     // FP32-flux forms: refresh the cached rates when u has moved
                     // by more than u_tol since they were computed (a rate change
                     // below a quarter ulp), or at the zone's first pass
-                    const bool refresh = PREC != kPrecFP64 && !(fabsf(S.u - S.u_ref) <= P.u_tol);
+                    const bool refresh = PREC != kPrecFP64 && (!P.rate_cache || !(fabsf(S.u - S.u_ref) <= P.u_tol));
                     flux_pass<PREC>(P, g, lane, G, cur, S.constant, S.s, S.u, S.poly, refresh);
                     gs.sync();
                     if (lane == 0 && refresh) S.u_ref = S.u;
@@ -895,7 +896,7 @@ __device__ void run_group(const PlanDev& P, const OptsDev& O, const unsigned cha
             if (spec && lane == 32) {
                 // the candidate state's profile factor (t + h) / (tau ln 2), once per group
                 S.u_spec = S.constant ? 0.f : __fmul_rn(__double2float_rn(S.t + h_now), S.u_scale);
-                S.refresh_spec = !(fabsf(S.u_spec - S.u_ref) <= P.u_tol);
+                S.refresh_spec = !P.rate_cache || !(fabsf(S.u_spec - S.u_ref) <= P.u_tol);
             }
             update_reduce<PREC>(P, O, g, lane, cur, h_now, z);
             gs.sync();

@@ -63,7 +63,7 @@ struct GroupLayout {
     int32_t off_V;      // real[R + S_r + 1]: fluxes f_j, partial planes 0, 1, 2 (reactions with
                         //   more than 0, 1, 2 reactants), constant 0
     int32_t off_K;      // real[R]: the zone's rates at (T0, rho0)
-    int32_t off_Kc;     // float[R] (FP32-flux forms): the rates at u_ref, K_j 2^(-c_j u_ref)
+    int32_t off_Kc;     // float[R] (FP32-flux forms with the rate cache): the rates at u_ref
     int32_t off_Y;      // FP64 and mixed-FP64: double[2][N + 1], entry N the constant 1; mixed:
                         //   float[2][N + 1], the low parts of the float-float abundances (0 at N)
     int32_t off_Y32;    // float[2][N + 1] (FP32-flux forms): the FP32 copy the flux pass reads (the
@@ -110,6 +110,7 @@ struct PlanDev {
     double cmax;                 // max_j c_j
     float u_tol;                 // FP32-flux forms: cached rates are reused while |u - u_ref| <= u_tol,
                                  //   i.e. while no rate would move by a quarter ulp: 2^-26 / (cmax ln 2)
+    int32_t rate_cache;          // 1: the groups keep the cache Kc (FP32-flux forms, small enough R)
     int32_t zero_idx;            // V index of the constant zero (= R + S_r)
     int32_t smem_tables;         // 1: stage blob into shared memory
     int32_t G, M;                // threads per zone group, groups per CTA
