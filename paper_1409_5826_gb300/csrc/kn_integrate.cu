@@ -341,15 +341,15 @@ __device__ __forceinline__ void update_reduce(const PlanDev& P, const OptsDev& O
 // lane 0, after the barrier that follows update_reduce: combine the warps.
 // A non-finite abundance makes the conservation sum non-finite, so the
 // finiteness test reads that sum.
-struct Verdict {
+struct TestOutcome {
     double cons, bn, bd;
     float rmax, cons32;
     int fin, pass;
 };
 template <int PREC>
-__device__ __forceinline__ Verdict combine(const PlanDev& P, const OptsDev& O, const GroupPtrs& g) {
+__device__ __forceinline__ TestOutcome combine(const PlanDev& P, const OptsDev& O, const GroupPtrs& g) {
     const int nw = P.G >> 5;
-    Verdict v{0.0, 0.0, 1.0, 0.f, 0.f, 1, 0};
+    TestOutcome v{0.0, 0.0, 1.0, 0.f, 0.f, 1, 0};
     if (PREC == kPrecMixed) {
         float ch = 0.f, cl = 0.f;
         int ok = 1;
@@ -860,7 +860,7 @@ __device__ void run_group(const PlanDev& P, const OptsDev& O, const unsigned cha
                         update_reduce<PREC>(P, O, g, lane, cur, hq, z);
                         gs.sync();
                         if (lane == 0) {
-                            const Verdict v = combine<PREC>(P, O, g);
+                            const TestOutcome v = combine<PREC>(P, O, g);
                             if (v.pass) label = (float)log(hq / S.h_prev);
                             S.found = !v.pass || last;  // stop
                         }
@@ -905,7 +905,7 @@ __device__ void run_group(const PlanDev& P, const OptsDev& O, const unsigned cha
             have_a = spec;
             if (lane == 0) {
                 if (spec && S.refresh_spec) S.u_ref = S.u_spec;  // the speculative pass refreshed Kc
-                const Verdict v = combine<PREC>(P, O, g);
+                const TestOutcome v = combine<PREC>(P, O, g);
                 const double h = S.h;
                 if (O.probe) {
                     O.probe_cons[z] = PREC == kPrecMixed ? (double)v.cons32 : v.cons;
