@@ -280,6 +280,36 @@ def size_sweep(args):
                       "rows": rows}), flush=True)
 
 
+def single_zone_configs():
+    """The measurement plan's single-zone configurations at constant T9 = 3,
+    rho = 1e8: the 16/48 chain and the 150/1604 network.  Time per accepted
+    step of one zone on the GPU (FP64 and mixed forms, fastest one-group
+    tiling), of the FP64 oracle on one host core and of dense-LU backward
+    Euler on one host core."""
+    import oracle
+    from kn_inputs import chain_network, constant_zones, net150
+    from paper_1409_5826_gb300 import kn, size_sweep as sw
+    out = {}
+    for name, net in (("chain16_48", chain_network()), ("net150_1604", net150())):
+        row = {}
+        for form, prec in (("fp64", kn.PREC_FP64), ("mixed", kn.PREC_MIXED)):
+            t = sw.single_zone_step_time(net, steps=2000, precision=prec, T9=3.0, rho=1e8)
+            row[f"gpu_{form}_s_per_step"] = t["s_per_step"]
+            row[f"gpu_{form}_threads_per_zone"] = t["threads_per_zone"]
+        orc = oracle.Oracle(net)
+        z = constant_zones(net, 1, T9=3.0, rho=1e8, t_end=sw.T_END)
+        t0 = time.perf_counter()
+        r = orc.integrate(z, 0, oracle.OracleOpts(max_steps=2000))
+        row["cpu_oracle_s_per_step"] = (time.perf_counter() - t0) / max(1, r["steps"])
+        t0 = time.perf_counter()
+        b = orc.be_integrate(z, 0, oracle.OracleOpts(max_steps=200 if net.n_species <= 64 else 30), max_iter=6)
+        row["cpu_backward_euler_s_per_step"] = (time.perf_counter() - t0) / max(1, b["steps"])
+        row["cores"] = 1
+        out[name] = row
+    out["conditions"] = "one zone, T9 = 3, rho = 1e8 constant, 2000 steps (backward Euler: 200 / 30)"
+    return out
+
+
 def _timed_form(kn, g, dz, stream, opts, reps=2):
     """One warm-up and `reps` timed batches of a form; returns (ms/batch, stats)."""
     import torch
@@ -528,6 +558,7 @@ def main():
             "clocks": clk, "e2e": e2e, "gpu_launches": 3 * args.steps, "roofline": roof}
     if not args.no_forms:
         line["forms"] = other_forms(kn, g, net, zones, dz, stream, st["steps"], kms)
+        line["single_zone"] = single_zone_configs()
     if not args.no_cpu:
         exp, be = cpu_baselines(net, zones)
         line["cpu_baseline"] = exp

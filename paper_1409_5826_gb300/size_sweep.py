@@ -22,11 +22,13 @@ RHO = 1e8
 T_END = 1e-3  # long enough that every run ends at its step limit
 
 
-def single_zone_step_time(net, steps: int = 2000, precision: int = kn.PREC_MIXED, stream=None) -> dict:
-    """One zone at (T9, RHO), `steps` attempts: the fastest one-group tiling's
-    time per accepted step and per attempt (CUDA events around the launch)."""
+def single_zone_step_time(net, steps: int = 2000, precision: int = kn.PREC_MIXED, stream=None,
+                          T9: float = T9, rho: float = RHO) -> dict:
+    """One zone at constant (T9, rho), `steps` attempts: the fastest one-group
+    tiling's time per accepted step and per attempt (CUDA events around the
+    launch)."""
     import torch
-    zones = constant_zones(net, 1, T9=T9, rho=RHO, t_end=T_END)
+    zones = constant_zones(net, 1, T9=T9, rho=rho, t_end=T_END)
     g = kn.Network(net)
     n = int(net.n_species)
     cands = sorted({min(1024, max(64, (n + 31) // 32 * 32)), 128, 256, 512, 1024})
