@@ -61,3 +61,27 @@ def test_zone_generators():
     assert (c.tau == 0).all() and c.n_zones == 3
     lab = mixed_assignment(2048)
     assert np.bincount(lab).tolist() == [512, 1024, 512]
+
+
+@pytest.mark.parametrize("n", [16, 32, 64, 100, 150, 250, 365])
+def test_sweep_networks(n):
+    from kn_inputs import SWEEP_SIZES, sweep_network
+    assert n in SWEEP_SIZES
+    a, b = sweep_network(n), sweep_network(n)
+    assert a.n_species == n
+    for f in ("A", "reac", "prod", "ln_k0", "t9_exp"):
+        assert np.array_equal(getattr(a, f), getattr(b, f))  # deterministic
+    for j in range(a.n_reactions):
+        r = a.reac[j][a.reac[j] >= 0]
+        p = a.prod[j][a.prod[j] >= 0]
+        assert 1 <= len(r) <= 3 and 1 <= len(p) <= 3
+        assert a.A[r].sum() == a.A[p].sum()
+    # the endpoints are the benchmark networks; sizes in between interpolate
+    # the reaction count between 10.69 and 12.05 per species
+    if n == 150:
+        assert a.n_reactions == 1604
+    elif n == 365:
+        assert a.n_reactions == 4400
+    elif n > 16:
+        assert 10.5 * n <= a.n_reactions <= 12.1 * n
+    assert abs(float((a.A * a.initial_Y()).sum()) - 1.0) < 1e-12
