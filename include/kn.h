@@ -59,7 +59,9 @@ typedef enum { KN_MEM_HOST = 0, KN_MEM_DEVICE = 1 } kn_mem;
 typedef enum {
     KN_PREC_FP64 = 0, /* every step of the path in FP64 */
     KN_PREC_MIXED = 1, /* FP32 rates, fluxes and gathers (every row sum of positive
-                          terms within (L + 5) 2^-24 relative, L <= the longest row);
+                          terms within (L + 5) 2^-24 relative, L <= the longest row;
+                          for networks of up to 2048 reactions the FP32 rates are
+                          cached and refreshed before any moves by 2^-26 relative);
                           abundances kept as FP32 high/low pairs (~48 bits); the
                           kappa-switched update in FP32; the conservation sum as a
                           float-float sum of exact products; the relative-error
