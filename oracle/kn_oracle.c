@@ -40,7 +40,9 @@
  *                   (the paper's Xnet is sparse; dense is the brute-force form).
  *
  * Parity pins (checked by the CPU test-suite, not by this file): hand-computed
- * single steps in exact rational arithmetic, the A<->B closed form, FE and
+ * single steps in exact rational arithmetic, hand-worked cases of or_test and
+ * or_growth and a hand-worked run of the step loop (each case built so that a
+ * plausible slip changes its outcome), the A<->B closed form, FE and
  * asymptotic linear maps against matrix powers, conservation of sum A_i Y_i,
  * equilibrium ratios of reversible pairs, positivity, rate scaling laws, and
  * backward Euler with Richardson extrapolation on tiny networks.
