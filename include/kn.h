@@ -382,9 +382,12 @@ kn_status kn_measure_fp64_peak(double *tflops, void *stream);
  * device and stall work the code overlaps with the network integration).
  *
  * Same integration as kn_integrate_batch for one network, but every zone
- * array is the caller's (device pointers, row-major as in
- * kn_zone_conditions / kn_get_abundances): zc holds the inputs; Y [n_zones]
- * [n_species] receives the abundances at t (Y0 is copied there first), t,
+ * array is the caller's (device memory of the current device, row-major as
+ * in kn_zone_conditions / kn_get_abundances; each pointer is checked on the
+ * host and anything else -- host memory, another device's memory -- is
+ * refused before any launch): zc holds the inputs; Y [n_zones][n_species]
+ * receives the abundances at t (Y0 is copied there first; Y may be Y0 itself,
+ * which integrates in place, but must not otherwise overlap it), t,
  * dt_next [n_zones] double, steps, rejects [n_zones] int64, status
  * [n_zones] int32.  The network's resident tables must already exist for
  * opts->precision and opts->threads_per_zone (built by any earlier
@@ -394,13 +397,14 @@ kn_status kn_measure_fp64_peak(double *tflops, void *stream);
  *
  * Its only scratch (work-queue counter and order) is a fixed device array in
  * the library, 256 KB per device: no call allocates device memory.  The
- * first call on each device looks up that array's address; make that first
+ * first call on each device (and again after the device's context changes,
+ * e.g. after cudaDeviceReset) looks up that array's address; make that first
  * call before any stream capture.  Every call shares the array and clears
  * what it needs, so calls whose GPU work overlaps (different streams or
  * threads) race: serialise them.  Asynchronous on `stream`.
- * Errors: KN_ERR_INVALID_ARG (NULL pointer, n_zones < 1 or above
- * KN_NOALLOC_MAX_ZONES, bad opts or tiling), KN_ERR_STATE (tables not built),
- * KN_ERR_CUDA.
+ * Errors: KN_ERR_INVALID_ARG (NULL or non-device pointer, Y partly
+ * overlapping Y0, n_zones < 1 or above KN_NOALLOC_MAX_ZONES, bad opts or
+ * tiling), KN_ERR_STATE (tables not built), KN_ERR_CUDA.
  */
 kn_status kn_integrate_noalloc(kn_network *net, int32_t n_zones, const kn_zone_conditions *zc,
                                const kn_opts *opts, double *Y, double *t, double *dt_next,

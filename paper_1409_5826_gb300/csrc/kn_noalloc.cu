@@ -15,11 +15,16 @@
 // holds the previous call's contents; each call clears the counters it needs.
 // Two calls whose work overlaps on the GPU (different streams, or threads)
 // race on it: serialise them on one stream.
+#include <cuda.h>
+
 #include <cstdint>
 #include <cstring>
+#include <mutex>
 
 #include "../../include/kn.h"
 #include "kn_internal.h"
+
+#include <cstdio>
 
 namespace kn {
 kn_status noalloc_prepare(kn_network* n, const kn_opts* o, int32_t n_zones, const kn_zone_conditions* zc,
@@ -46,8 +51,35 @@ constexpr int kScratchInts = kOffMinMax + 2;
 
 static __device__ __align__(256) int g_scratch[kScratchInts];
 
-// Address of g_scratch on each device, set once per device on first use.
-static int* g_scratch_addr[64];
+// Address of g_scratch on each device, looked up on the first call with that
+// device current and again whenever the device's current context differs from
+// the one the address was taken in (after cudaDeviceReset the old address is
+// stale).  Guarded so that threads racing on a device's first call agree.
+struct ScratchAddr {
+    CUcontext ctx = nullptr;
+    int* addr = nullptr;
+};
+static ScratchAddr g_scratch_addr[64];
+static std::mutex g_scratch_mu;
+
+// The calling thread's current context, through the driver entry point the
+// runtime hands out (the library does not link the driver library itself).
+static CUcontext current_context() {
+    typedef CUresult (*GetCurrent)(CUcontext*);
+    static GetCurrent fn = nullptr;
+    static bool looked = false;
+    if (!looked) {
+        void* p = nullptr;
+        cudaDriverEntryPointQueryResult q;
+        if (cudaGetDriverEntryPointByVersion("cuCtxGetCurrent", &p, 12000, cudaEnableDefault, &q) == cudaSuccess &&
+            q == cudaDriverEntryPointSuccess)
+            fn = (GetCurrent)p;
+        looked = true;
+    }
+    CUcontext c = nullptr;
+    if (!fn || fn(&c) != CUDA_SUCCESS) c = nullptr;
+    return c;
+}
 
 __device__ __forceinline__ unsigned int key_bits(float f) {
     const unsigned int u = __float_as_uint(f);
@@ -117,20 +149,38 @@ __global__ void noalloc_scatter(const double* T0, const double* rho0, int n, dou
     }
 }
 
-// Once per device, with that device current: the device address of g_scratch.
+// Once per device (and context), with that device current: the device address
+// of g_scratch.  In host code the name g_scratch is only a host-side stand-in.
 static kn_status scratch_address(int** out) {
     int dev = 0;
     cudaError_t e = cudaGetDevice(&dev);
     if (e != cudaSuccess) return noalloc_fail(KN_ERR_CUDA, cudaGetErrorString(e));
     if (dev < 0 || dev >= 64) return noalloc_fail(KN_ERR_INVALID_ARG, "kn_integrate_noalloc: device id out of range");
-    if (!g_scratch_addr[dev]) {
+    std::lock_guard<std::mutex> lock(g_scratch_mu);
+    CUcontext ctx = current_context();
+    ScratchAddr& a = g_scratch_addr[dev];
+    if (!a.addr || !ctx || ctx != a.ctx) {
         void* p = nullptr;
-        e = cudaGetSymbolAddress(&p, g_scratch);
+        e = cudaGetSymbolAddress(&p, g_scratch);  // makes the device's context current if it was not
         if (e != cudaSuccess || !p) return noalloc_fail(KN_ERR_CUDA, "cudaGetSymbolAddress(g_scratch) failed");
-        g_scratch_addr[dev] = (int*)p;
+        ctx = current_context();
+        a.addr = (int*)p;
+        a.ctx = ctx;
     }
-    *out = g_scratch_addr[dev];
+    *out = a.addr;
     return KN_OK;
+}
+
+// A pointer the integrator may dereference: device (or managed) memory of the
+// current device.  Host memory, and memory of another device, are refused on
+// the host before any launch.
+static bool on_current_device(const void* p, int dev) {
+    cudaPointerAttributes at;
+    if (cudaPointerGetAttributes(&at, p) != cudaSuccess) {
+        cudaGetLastError();  // the failed query's error is not sticky: clear it
+        return false;
+    }
+    return (at.type == cudaMemoryTypeDevice || at.type == cudaMemoryTypeManaged) && at.device == dev;
 }
 
 }  // namespace
@@ -150,6 +200,22 @@ extern "C" kn_status kn_integrate_noalloc(kn_network* net, int32_t n_zones, cons
     int* scratch = nullptr;
     kn_status s = scratch_address(&scratch);
     if (s != KN_OK) return s;
+    {
+        int dev = 0;
+        cudaError_t e = cudaGetDevice(&dev);
+        if (e != cudaSuccess) return noalloc_fail(KN_ERR_CUDA, cudaGetErrorString(e));
+        const void* ptrs[13] = {zc->Y0, zc->T0, zc->rho0, zc->tau, zc->t_start, zc->t_end, zc->dt_trial,
+                                Y, t, dt_next, steps, rejects, status};
+        static const char* names[13] = {"Y0", "T0", "rho0", "tau", "t_start", "t_end", "dt_trial",
+                                        "Y", "t", "dt_next", "steps", "rejects", "status"};
+        for (int k = 0; k < 13; ++k)
+            if (!on_current_device(ptrs[k], dev)) {
+                char msg[160];
+                snprintf(msg, sizeof msg,
+                         "kn_integrate_noalloc: %s is not device memory of the current device", names[k]);
+                return noalloc_fail(KN_ERR_INVALID_ARG, msg);
+            }
+    }
     LaunchParams lp;
     int grid = 0, block = 0, n_species = 0;
     double nbar = 0, rbar = 0;
@@ -157,9 +223,17 @@ extern "C" kn_status kn_integrate_noalloc(kn_network* net, int32_t n_zones, cons
                         scratch + kOffHead, lp, grid, block, nbar, rbar);
     if (s != KN_OK) return s;
     n_species = lp.plans[0].N;
-    cudaError_t e = cudaMemcpyAsync(Y, zc->Y0, sizeof(double) * (size_t)n_zones * n_species,
-                                    cudaMemcpyDeviceToDevice, st);
-    if (e != cudaSuccess) return noalloc_fail(KN_ERR_CUDA, cudaGetErrorString(e));
+    // Y may be Y0 itself (integrated in place); any other overlap is refused
+    const size_t ybytes = sizeof(double) * (size_t)n_zones * n_species;
+    const char* yb = (const char*)Y;
+    const char* y0b = (const char*)zc->Y0;
+    cudaError_t e = cudaSuccess;
+    if (yb != y0b) {
+        if (yb < y0b + ybytes && y0b < yb + ybytes)
+            return noalloc_fail(KN_ERR_INVALID_ARG, "kn_integrate_noalloc: Y overlaps Y0 without being Y0");
+        e = cudaMemcpyAsync(Y, zc->Y0, ybytes, cudaMemcpyDeviceToDevice, st);
+        if (e != cudaSuccess) return noalloc_fail(KN_ERR_CUDA, cudaGetErrorString(e));
+    }
     const int nb = (n_zones + 255) / 256;
     noalloc_clear<<<1, 2 * kBuckets, 0, st>>>();
     noalloc_minmax<<<nb, 256, 0, st>>>(zc->T0, zc->rho0, n_zones, nbar, rbar);

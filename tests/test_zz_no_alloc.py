@@ -77,20 +77,89 @@ def test_noalloc_matches_batch_on_two_calls(env, prec):
     g.close()
 
 
-def test_noalloc_refuses_oversize_and_unbuilt_tables(env):
+def _zone_buffers(torch, Z, N):
+    """Device inputs and outputs sized for Z zones of N species, so that a
+    call that wrongly got past the host checks would still stay in bounds."""
+    dev = torch.device("cuda")
+    zin = {k: torch.zeros((Z, N) if k == "Y0" else (Z,), dtype=torch.float64, device=dev) for k in NAMES}
+    return zin, _outputs(torch, Z, N)
+
+
+def test_noalloc_refuses_oversize_unbuilt_tables_and_host_memory(env):
     torch, kn = env
     net = net150()
+    N = net.n_species
     g = kn.Network(net)
     L = kn.lib()
-    dummy = torch.zeros(8, dtype=torch.float64, device="cuda")
-    zc = kn._Zones(*([dummy.data_ptr()] * 7))
-    ptrs = [dummy.data_ptr()] * 6
     opts = kn.Opts(precision=1, threads_per_zone=160, threads_per_cta=160)
-    rc = L.kn_integrate_noalloc(g.h, 65537, C.byref(zc), C.byref(opts.c()), *ptrs, None)
+    # one zone over the limit, with buffers of that size
+    Z = 65537
+    zin, out = _zone_buffers(torch, Z, N)
+    zc = kn._Zones(*[zin[k].data_ptr() for k in NAMES])
+    rc = L.kn_integrate_noalloc(g.h, Z, C.byref(zc), C.byref(opts.c()), *[out[k].data_ptr() for k in OUTS], None)
     assert rc == kn.KN_ERR_INVALID_ARG
     assert b"KN_NOALLOC_MAX_ZONES" in L.kn_last_error()
+    del zin, out
     # a network whose tables were never built for these opts
-    rc = L.kn_integrate_noalloc(g.h, 4, C.byref(zc), C.byref(opts.c()), *ptrs, None)
+    Z = 4
+    zin, out = _zone_buffers(torch, Z, N)
+    zc = kn._Zones(*[zin[k].data_ptr() for k in NAMES])
+    rc = L.kn_integrate_noalloc(g.h, Z, C.byref(zc), C.byref(opts.c()), *[out[k].data_ptr() for k in OUTS], None)
     assert rc == kn.KN_ERR_STATE
     assert b"not built" in L.kn_last_error()
+    # build the tables, then hand it host memory: refused on the host, no launch
+    z = profile_zones(net, Z, t_end=3e-11)
+    g.set_zones(z)
+    kn.integrate_batch([g], opts)
+    torch.cuda.synchronize()
+    host_Y = np.zeros((Z, N))
+    ptrs = [out[k].data_ptr() for k in OUTS]
+    ptrs[0] = host_Y.ctypes.data
+    rc = L.kn_integrate_noalloc(g.h, Z, C.byref(zc), C.byref(opts.c()), *ptrs, None)
+    assert rc == kn.KN_ERR_INVALID_ARG
+    assert b"Y is not device memory" in L.kn_last_error()
+    host_T0 = np.ones(Z)
+    zc_host = kn._Zones(*[host_T0.ctypes.data if k == "T0" else zin[k].data_ptr() for k in NAMES])
+    rc = L.kn_integrate_noalloc(g.h, Z, C.byref(zc_host), C.byref(opts.c()),
+                                *[out[k].data_ptr() for k in OUTS], None)
+    assert rc == kn.KN_ERR_INVALID_ARG
+    assert b"T0 is not device memory" in L.kn_last_error()
+    # Y overlapping Y0 without being Y0 (shifted by one species)
+    big = torch.zeros((Z + 1) * N, dtype=torch.float64, device="cuda")
+    zc_ov = kn._Zones(*[big.data_ptr() if k == "Y0" else zin[k].data_ptr() for k in NAMES])
+    ptrs = [out[k].data_ptr() for k in OUTS]
+    ptrs[0] = big.data_ptr() + 8
+    rc = L.kn_integrate_noalloc(g.h, Z, C.byref(zc_ov), C.byref(opts.c()), *ptrs, None)
+    assert rc == kn.KN_ERR_INVALID_ARG
+    assert b"overlaps" in L.kn_last_error()
+    torch.cuda.synchronize()
+    g.close()
+
+
+def test_noalloc_in_place(env):
+    """Y may be Y0 itself: the zones integrate in place and match the batch."""
+    torch, kn = env
+    net = net150()
+    Z = 64
+    z = profile_zones(net, Z, t_end=3e-11)
+    opts = kn.Opts(precision=1, threads_per_zone=160, threads_per_cta=800)
+    g = kn.Network(net)
+    g.set_zones(z)
+    kn.integrate_batch([g], opts)
+    ref = g.get()
+    dev = torch.device("cuda")
+    dz = {k: torch.from_numpy(np.ascontiguousarray(getattr(z, k))).to(dev) for k in NAMES}
+    zc = kn._Zones(*[dz[k].data_ptr() for k in NAMES])
+    out = _outputs(torch, Z, net.n_species)
+    ptrs = [out[k].data_ptr() for k in OUTS]
+    ptrs[0] = dz["Y0"].data_ptr()
+    L = kn.lib()
+    rc = L.kn_integrate_noalloc(g.h, Z, C.byref(zc), C.byref(opts.c()), *ptrs,
+                                C.c_void_p(torch.cuda.current_stream().cuda_stream))
+    assert rc == kn.KN_OK, L.kn_last_error()
+    torch.cuda.synchronize()
+    Y = dz["Y0"].cpu().numpy()
+    assert np.array_equal(out["steps"].cpu().numpy(), ref["steps"])
+    m = ref["Y"] > 1e-30
+    assert np.max(np.abs(Y[m] - ref["Y"][m]) / ref["Y"][m]) <= 1e-12
     g.close()
