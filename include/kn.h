@@ -170,7 +170,35 @@ typedef struct {
     int64_t record_capacity;
     int64_t *record_count;
     double mlp_margin;        /* ln-units safety margin of the learned proposal, default 0.5 */
-    int64_t reserved[3];
+    /* Trace of the learned proposal (validation; needs mlp): every time the
+       network proposes a step, one record is appended:
+         trace_features [cap][64]  the features it was given (FP32)
+         trace_out [cap]           its output (FP32)
+         trace_dt [cap][6]         dt_prev; dt_plain; the unclipped proposal
+                                   dt_prev e^min(out - mlp_margin, 20); the step
+                                   the attempt then takes; 1 if that step is the
+                                   proposal, else 0; t_end - t
+       *trace_count (device, zeroed by the caller) counts every record; those
+       beyond trace_capacity are counted but not written.  NULL = off. */
+    float *trace_features;
+    float *trace_out;
+    double *trace_dt;
+    int64_t trace_capacity;
+    int64_t *trace_count;
+    /* Perfect-proposal run (measurement; needs record_features): at every state
+       reached by an accepted step, the attempt takes the step of the record's
+       label -- the last grid step before the first that fails the accept test
+       from that state -- clipped to [dt_plain, 16 dt_plain] like a learned
+       proposal with margin 0, and falls back to dt_plain if that step is not
+       above it.  Its step count bounds what any learned proposal of this form
+       can save.  0 = off. */
+    int32_t follow_label;
+    int32_t pad_;
+    /* Per-zone timing (measurement): zone_ns [total zones][2] (device int64)
+       receives the GPU global timer, in ns, when a zone group takes the zone
+       from the work queue and when it has written the zone back.  Zones are
+       numbered across the nets of the call in order.  NULL = off. */
+    int64_t *zone_ns;
 } kn_opts;
 
 /* Aggregate counters of the last kn_integrate_batch on these networks. */
@@ -316,14 +344,17 @@ kn_status kn_mlp_set_params(kn_mlp *mlp, const float *params, const float *mu, c
    KN_MLP_PARAMS (either may be NULL).  Synchronises the device. */
 kn_status kn_mlp_get_params(const kn_mlp *mlp, float *params, float *grads);
 
-/* Inference on a batch: features [B][64] and out [B] are device FP32 arrays.
-   Asynchronous on `stream`.  Errors: KN_ERR_INVALID_ARG, KN_ERR_CUDA. */
+/* Inference on a batch: features [B][64] and out [B] are device FP32 arrays
+   (features 16-byte aligned).  Asynchronous on `stream`.
+   Errors: KN_ERR_INVALID_ARG, KN_ERR_CUDA. */
 kn_status kn_mlp_forward(kn_mlp *mlp, const float *features, int32_t B, float *out, void *stream);
 
 /* Forward and backward pass of the mean squared error against labels [B]
-   (device FP32); the gradients stay in the handle for kn_mlp_adam, and the
-   loss is written to *loss (device FP32 scalar) when loss is not NULL.
-   Asynchronous on `stream`. */
+   (device FP32; features as for kn_mlp_forward); the gradients stay in the
+   handle for kn_mlp_adam, and the loss is written to *loss (device FP32
+   scalar) when loss is not NULL.  Tiles of 64 rows are processed by one CTA
+   each and their partial gradients added in a fixed order, so a call is
+   deterministic.  Asynchronous on `stream`. */
 kn_status kn_mlp_backward(kn_mlp *mlp, const float *features, const float *labels, int32_t B, float *loss,
                           void *stream);
 

@@ -368,6 +368,13 @@ static kn_status validate_opts(const kn_opts* o) {
         return fail(KN_ERR_INVALID_ARG, "opts.record_features needs record_labels, record_count, capacity >= 0");
     if (o->record_features && o->mlp)
         return fail(KN_ERR_INVALID_ARG, "opts.record_features and opts.mlp are not combined");
+    if (o->trace_features || o->trace_out || o->trace_dt || o->trace_count) {
+        if (!o->mlp) return fail(KN_ERR_INVALID_ARG, "opts.trace_* needs opts.mlp");
+        if (!o->trace_features || !o->trace_out || !o->trace_dt || !o->trace_count || o->trace_capacity < 0)
+            return fail(KN_ERR_INVALID_ARG, "opts.trace_* must be set together, with trace_capacity >= 0");
+    }
+    if (o->follow_label && !o->record_features)
+        return fail(KN_ERR_INVALID_ARG, "opts.follow_label needs opts.record_features");
     if ((o->replay_dt != nullptr) != (o->replay_off != nullptr) ||
         (o->replay_dt != nullptr) != (o->replay_len != nullptr))
         return fail(KN_ERR_INVALID_ARG, "opts.replay_dt/off/len must be set together");
@@ -579,6 +586,7 @@ static kn_status prepare_launch(kn_network* const* nets, int n_nets, const kn_op
     D.max_reject = o->max_reject;
     D.lockstep = o->lockstep;
     set_guard_band(D, o);
+    D.zone_ns = probe ? nullptr : (long long*)o->zone_ns;
     D.replay_dt = o->replay_dt;
     D.replay_off = (const long long*)o->replay_off;
     D.replay_len = (const long long*)o->replay_len;
@@ -588,6 +596,13 @@ static kn_status prepare_launch(kn_network* const* nets, int n_nets, const kn_op
         const void* W;
         mlp_device_view(o->mlp, &D.mlpP, &W, &D.mlpNorm);
         D.mlpW = W;
+        if (o->trace_features) {
+            D.trace_feat = o->trace_features;
+            D.trace_out = o->trace_out;
+            D.trace_dt = o->trace_dt;
+            D.trace_cap = o->trace_capacity;
+            D.trace_count = (unsigned long long*)o->trace_count;
+        }
     }
     if (record) {
         D.record = 1;
@@ -595,6 +610,7 @@ static kn_status prepare_launch(kn_network* const* nets, int n_nets, const kn_op
         D.rec_label = o->record_labels;
         D.rec_cap = o->record_capacity;
         D.rec_count = (unsigned long long*)o->record_count;
+        D.follow_label = o->follow_label ? 1 : 0;
     }
     return KN_OK;
 }

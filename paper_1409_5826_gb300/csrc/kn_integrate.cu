@@ -42,6 +42,12 @@ struct GroupSync {
     }
 };
 
+__device__ __forceinline__ long long global_ns() {
+    unsigned long long t;
+    asm volatile("mov.u64 %0, %%globaltimer;" : "=l"(t));
+    return (long long)t;
+}
+
 __device__ __forceinline__ float ex2_approx(float x) {
     float y;
     asm("ex2.approx.ftz.f32 %0, %1;" : "=f"(y) : "f"(x));
@@ -654,6 +660,7 @@ __device__ void run_group(const PlanDev& P, const OptsDev& O, const unsigned cha
             const int q = atomicAdd(P.queue_head, 1);
             S.zone = q < P.n_zones ? P.order[q] : -1;
             S.valid = 1;
+            if (O.zone_ns) S.t_fetch_ns = global_ns();
         }
         gs.sync();
         const int z = S.zone;
@@ -852,6 +859,7 @@ __device__ void run_group(const PlanDev& P, const OptsDev& O, const unsigned cha
                     // smallest step; the label is the last step before the first
                     // failure (or the step that reaches t_end)
                     float label = -1.3862943611198906f;
+                    if (lane == 0) S.h_best = 0.0;
                     for (int q = -8; q <= 16; ++q) {
                         double hq = S.h_prev * exp2(0.25 * q);
                         const double rem = S.t_end - S.t;
@@ -861,13 +869,30 @@ __device__ void run_group(const PlanDev& P, const OptsDev& O, const unsigned cha
                         gs.sync();
                         if (lane == 0) {
                             const TestOutcome v = combine<PREC>(P, O, g);
-                            if (v.pass) label = (float)log(hq / S.h_prev);
+                            if (v.pass) {
+                                label = (float)log(hq / S.h_prev);
+                                S.h_best = hq;
+                            }
                             S.found = !v.pass || last;  // stop
                         }
                         gs.sync();
                         if (S.found) break;
                     }
-                    if (lane == 0) write_record(O, g, label);
+                    if (lane == 0) {
+                        write_record(O, g, label);
+                        if (O.follow_label) {
+                            // the perfect proposal: the label's step, clipped like a learned one
+                            const double lo = S.dt_plain, hi = 16.0 * S.dt_plain;
+                            double hb = S.h_best;
+                            if (hb > lo) {
+                                hb = hb > hi ? hi : hb;
+                                const double rem = S.t_end - S.t;
+                                S.clipped = hb >= rem;
+                                S.h = S.clipped ? rem : hb;
+                                S.mlp_try = S.h > lo;
+                            }
+                        }
+                    }
                 }
                 if (O.learn) {
                     const float out = mlp_forward_group(O, g, mlp_smem, lane, G, gs);
@@ -876,12 +901,28 @@ __device__ void run_group(const PlanDev& P, const OptsDev& O, const unsigned cha
                         double hm = S.h_prev * (double)expf(fminf(out - O.mlp_margin, 20.f));
                         const double lo = S.dt_plain, hi = 16.0 * S.dt_plain;
                         // a proposal at or below the plain step is the plain attempt itself
+                        const double raw = hm;
                         if (hm > lo) {
                             hm = hm > hi ? hi : hm;
                             const double rem = S.t_end - S.t;
                             S.clipped = hm >= rem;
                             S.h = S.clipped ? rem : hm;
                             S.mlp_try = S.h > lo;  // clipping to t_end can leave only the plain step
+                        }
+                        if (O.trace_out) {
+                            const unsigned long long slot = atomicAdd(O.trace_count, 1ull);
+                            if ((long long)slot < O.trace_cap) {
+                                float* f = O.trace_feat + slot * 64;
+                                for (int k = 0; k < 64; ++k) f[k] = g.feat[k];
+                                O.trace_out[slot] = out;
+                                double* d = O.trace_dt + slot * 6;
+                                d[0] = S.h_prev;
+                                d[1] = S.dt_plain;
+                                d[2] = raw;
+                                d[3] = S.h;
+                                d[4] = S.mlp_try ? 1.0 : 0.0;
+                                d[5] = S.t_end - S.t;
+                            }
                         }
                     }
                 }
@@ -1003,6 +1044,11 @@ __device__ void run_group(const PlanDev& P, const OptsDev& O, const unsigned cha
                 P.rejects[z] = S.rejects;
                 if (P.props) P.props[z] = S.props;
                 P.status[z] = S.status;
+                if (O.zone_ns) {
+                    long long* tz = O.zone_ns + 2 * (size_t)(P.zone_base + z);
+                    tz[0] = S.t_fetch_ns;
+                    tz[1] = global_ns();
+                }
             }
         }
         gs.sync();

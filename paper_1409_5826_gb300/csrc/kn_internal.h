@@ -98,6 +98,8 @@ struct GroupState {
     float u_scale;     // FP32-flux forms: 1/(tau ln 2)
     float u_ref;       // FP32-flux forms: the u at which the cached rates Kc were computed
     int refresh_spec;  // the speculative flux pass recomputes Kc
+    double h_best;     // label search: the last grid step that passed (0: none)
+    long long t_fetch_ns;  // global timer when the zone was taken from the queue
 };
 
 struct PlanDev {
@@ -169,6 +171,14 @@ struct OptsDev {
     float eps_r32, ymin_lo32, ymin_hi32, band_lo32, band_hi32, kappa32;
     float eps_c32, ga32, gb32, grow32;  // mixed form: eps_c and the growth factor's terms in FP32
     float thr_lo32, thr_hi32;           // mixed form: eps_r times the guard band's ends
+    // trace of the learned proposal: features [cap][64], output [cap], dt record [cap][6]
+    float* trace_feat;
+    float* trace_out;
+    double* trace_dt;
+    long long trace_cap;
+    unsigned long long* trace_count;
+    int follow_label;  // records: the attempt takes the label's step (perfect proposal)
+    long long* zone_ns;  // [zones][2]: global timer at queue fetch and at write-back (NULL: off)
     int learn;   // 1: propose with the network
     int record;  // 1: write (features, label) at every accepted state
     int mlp_smem_off;  // byte offset of the staged network in the CTA's shared memory

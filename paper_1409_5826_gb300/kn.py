@@ -51,7 +51,9 @@ class _Opts(C.Structure):
                 ("replay_dt", C.c_void_p), ("replay_off", C.c_void_p), ("replay_len", C.c_void_p),
                 ("mlp", C.c_void_p), ("record_features", C.c_void_p), ("record_labels", C.c_void_p),
                 ("record_capacity", C.c_int64), ("record_count", C.c_void_p), ("mlp_margin", C.c_double),
-                ("reserved", C.c_int64 * 3)]
+                ("trace_features", C.c_void_p), ("trace_out", C.c_void_p), ("trace_dt", C.c_void_p),
+                ("trace_capacity", C.c_int64), ("trace_count", C.c_void_p), ("follow_label", C.c_int32),
+                ("pad_", C.c_int32), ("zone_ns", C.c_void_p)]
 
 
 class _Stats(C.Structure):
@@ -156,8 +158,16 @@ class Opts:
     record_capacity: int = 0
     record_count: int = 0
     mlp_margin: float = 0.5
+    trace_features: int = 0
+    trace_out: int = 0
+    trace_dt: int = 0
+    trace_capacity: int = 0
+    trace_count: int = 0
+    follow_label: int = 0
+    zone_ns: int = 0
 
-    _PTRS = ("replay_dt", "replay_off", "replay_len", "mlp", "record_features", "record_labels", "record_count")
+    _PTRS = ("replay_dt", "replay_off", "replay_len", "mlp", "record_features", "record_labels", "record_count",
+             "trace_features", "trace_out", "trace_dt", "trace_count", "zone_ns")
 
     def c(self) -> _Opts:
         o = _Opts()

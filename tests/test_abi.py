@@ -35,7 +35,7 @@ def test_default_opts_match_header(knmod):
 
 def test_struct_sizes_match_header(knmod):
     # the binding's ctypes mirrors must match the C layouts byte for byte
-    assert C.sizeof(knmod._Opts) == 4 * 2 + 8 * 8 + 8 + 4 * 4 + 8 * 3 + 8 + 8 * 8
+    assert C.sizeof(knmod._Opts) == 4 * 2 + 8 * 8 + 8 + 4 * 4 + 8 * 3 + 8 + 8 * 5 + 8 * 5 + 4 * 2 + 8
     assert C.sizeof(knmod._Desc) == 8 + 5 * 8
     assert C.sizeof(knmod._Zones) == 7 * 8
 

@@ -97,6 +97,129 @@ def test_records_match_oracle(env, oracle_mod, which):
     g.close()
 
 
+def _bf16(x):
+    """Round to the nearest BF16 (ties to even), returned as float64."""
+    b = np.asarray(x, np.float32).view(np.uint32).astype(np.uint64)
+    r = ((b + 0x7FFF + ((b >> 16) & 1)) >> 16) << 16
+    return r.astype(np.uint32).view(np.float32).astype(np.float64)
+
+
+@pytest.mark.parametrize("margin", [0.0, 0.5])
+def test_in_integrator_inference_matches_oracle(env, margin):
+    """The network evaluation the integrator itself runs (shared-memory BF16
+    weights, FP32 accumulation on CUDA cores, one row per zone group) and
+    the proposal rule dt = clip(dt_prev e^(out - margin), dt_plain, 16
+    dt_plain), then clipped to t_end, element by element against the
+    oracle, from the integrator's own trace of every proposal."""
+    torch, kn, learned = env
+    rng = np.random.default_rng(11)
+    p = M.init_params(11)
+    for k in ("b1", "b2", "b3"):
+        p[k] = rng.normal(0, 0.1, p[k].shape)
+    p["b3"][:] = 0.3  # proposals on both sides of the plain step
+    mu = rng.normal(0, 1, 64).astype(np.float32)
+    mu[:4] = (1.3, 18.0, -25.0, 0.5)
+    sigma = np.full(64, 8.0, np.float32)
+    mlp = kn.MLP()
+    flat = kn.mlp_pack(p)
+    mlp.set_params(flat, mu, sigma)
+    pf = kn.mlp_unpack(flat)  # the FP32 values the GPU holds
+    net = net150()
+    z = profile_zones(net, 12, base_seed=77_000, t_end=1e-10)
+    g = kn.Network(net)
+    g.set_zones(z)
+    dev = torch.device("cuda")
+    cap = 200_000
+    tf = torch.full((cap, 64), float("nan"), dtype=torch.float32, device=dev)
+    to = torch.full((cap,), float("nan"), dtype=torch.float32, device=dev)
+    td = torch.full((cap, 6), float("nan"), dtype=torch.float64, device=dev)
+    tc = torch.zeros(1, dtype=torch.int64, device=dev)
+    o = kn.Opts(precision=kn.PREC_MIXED, mlp=mlp, mlp_margin=margin, trace_features=tf.data_ptr(),
+                trace_out=to.data_ptr(), trace_dt=td.data_ptr(), trace_capacity=cap, trace_count=tc.data_ptr())
+    kn.integrate_batch([g], o)
+    r = g.get()
+    assert (r["status"] == 0).all()
+    n = int(tc.item())
+    assert 1000 < n <= cap, n
+    feat = tf[:n].cpu().numpy()
+    out = to[:n].cpu().numpy().astype(np.float64)
+    d = td[:n].cpu().numpy()
+    assert np.isfinite(feat).all() and np.isfinite(out).all()
+    # (1) the network output, against the oracle on the BF16 operands the
+    # integrator uses (inputs, weights and hidden activations rounded to BF16)
+    inv = (np.float32(1.0) / sigma).astype(np.float32)
+    xs = ((feat - mu) * inv).astype(np.float32)
+    X = _bf16(xs)
+    h1 = _bf16(np.maximum(X @ _bf16(pf["W1"]) + pf["b1"], 0))
+    h2 = _bf16(np.maximum(h1 @ _bf16(pf["W2"]) + pf["b2"], 0))
+    ref = (h2 @ pf["W3"])[:, 0] + pf["b3"][0]
+    scale = max(1.0, np.max(np.abs(ref)))
+    err = np.abs(out - ref)
+    # equal up to FP32 summation order ...
+    assert np.mean(err <= 1e-5 * scale) >= 0.98, np.mean(err <= 1e-5 * scale)
+    # ... which can flip the BF16 rounding of a hidden activation by one BF16
+    # spacing (at most 2^-7 of its value).  Per row, one flip in h1 moves the
+    # output by at most 2^-7 |h1_k| sum_n |W2_kn w3_n|, one flip in h2 by
+    # 2^-7 |h2_n w3_n|; the rows that differ must stay within twice the sum.
+    w2w3 = np.abs(_bf16(pf["W2"])) @ np.abs(pf["W3"][:, 0])
+    flip = 2.0 ** -7 * (np.max(np.abs(h1) * w2w3, axis=1) + np.max(np.abs(h2 * pf["W3"][:, 0]), axis=1))
+    bad = err > 1e-5 * scale
+    assert np.all(err[bad] <= 2.0 * flip[bad] + 1e-5 * scale), np.max(err[bad] / flip[bad])
+    # and against the plain FP64 network on unrounded inputs (BF16 effects only)
+    ref64, _ = M.forward(pf, xs.astype(np.float64))
+    assert np.linalg.norm(out - ref64) <= 2e-2 * np.linalg.norm(ref64)
+    # (2) the proposal rule: dt_prev e^min(out - margin, 20) (FP32 exponential)
+    h_prev, dt_plain, raw, step, used, rem = d.T
+    e = np.exp(np.minimum(out.astype(np.float32) - np.float32(margin), np.float32(20.0)).astype(np.float64))
+    assert np.allclose(raw, h_prev * e, rtol=4e-7, atol=0)
+    # then exactly: clip to [dt_plain, 16 dt_plain], then to t_end; a proposal
+    # not above dt_plain leaves the plain attempt min(dt_plain, t_end - t)
+    prop = np.minimum(raw, 16.0 * dt_plain)
+    want_step = np.where(raw > dt_plain, np.minimum(prop, rem), np.minimum(dt_plain, rem))
+    want_used = (raw > dt_plain) & (want_step > dt_plain)
+    assert np.array_equal(step, want_step)
+    assert np.array_equal(used.astype(bool), want_used)
+    assert want_used.any() and (~want_used).any()
+    assert kn.batch_stats([g])["proposals_used"] <= int(want_used.sum())
+    mlp.close()
+    g.close()
+
+
+def test_perfect_proposal_follows_the_label(env, oracle_mod):
+    """follow_label: every state reached by an accepted step tries the
+    label's step (the largest grid step before the first failing one),
+    which passed the test from that very state, so no proposal of the run
+    is rejected.  The run is the measured ceiling of a learned proposal."""
+    torch, kn, learned = env
+    net = net150()
+    z = profile_zones(net, 16, base_seed=31_000, t_end=3e-11)
+    g = kn.Network(net)
+    dev = torch.device("cuda")
+    res = {}
+    for follow in (0, 1):
+        g.set_zones(z)
+        cap = 100_000
+        feat = torch.empty((cap, 64), dtype=torch.float32, device=dev)
+        lab = torch.empty(cap, dtype=torch.float32, device=dev)
+        cnt = torch.zeros(1, dtype=torch.int64, device=dev)
+        kn.integrate_batch([g], kn.Opts(precision=kn.PREC_FP64, record_features=feat.data_ptr(),
+                                        record_labels=lab.data_ptr(), record_capacity=cap,
+                                        record_count=cnt.data_ptr(), follow_label=follow))
+        r = g.get()
+        res[follow] = (r, kn.batch_stats([g]))
+        assert (r["status"] == 0).all() and np.array_equal(r["t"], z.t_end)
+    plain, ceil = res[0], res[1]
+    # the ceiling run takes the label's step wherever it beats the plain one,
+    # and needs no more steps than the plain controller
+    assert ceil[1]["proposals_used"] > 0
+    assert ceil[0]["steps"].sum() <= plain[0]["steps"].sum()
+    # same accuracy contract as the plain controller: the free-running tier
+    ref = oracle_mod.Oracle(net).integrate_batch(z, threads=8)
+    m = ref["Y"] > 1e-10
+    assert np.max(np.abs(ceil[0]["Y"][m] - ref["Y"][m]) / ref["Y"][m]) < 10 * 0.05
+    g.close()
+
+
 def _train_small(torch, kn, learned, n_zones=48, epochs=3, capacity=400_000):
     net = net150()
     jobs = [(net, profile_zones(net, n_zones, base_seed=500_000, t_end=1e-10)),
