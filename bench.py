@@ -9,8 +9,15 @@ persistent integrator (rates, fluxes, gathers, kappa-switched update, accept
 test, dt control) until every zone reaches t_end.
 
 Prints ONE JSON line (rank 0).  value = accepted zone-steps per second over
-all ranks; zones_per_s alongside.  --impl reference times the CPU FP64
-oracle instead (bounded sample of the same workload on the host cores).
+all ranks; zones_per_s alongside.  Beside the headline (the mixed form), each
+other form is timed the same way -- warm-up steps, CUDA events on the
+launching stream around each batch, the L2 flushed between batches, clocks
+sampled during the timed batches -- and carries its own roofline: the FP64
+form, the mixed form with the FP64 update, the mixed form with the learned
+proposal, the uneven-size batch (16/48 : 150/1604 : 365/4400 = 1:2:1), the
+perfect-proposal run that bounds any learned proposal, and the learned
+network's training kernels.  --impl reference times the CPU FP64 oracle
+instead (bounded sample of the same workload on the host cores).
 """
 import argparse
 import json
@@ -29,6 +36,9 @@ METRIC = "zone-steps/s and zones/s to t_end, 150sp/1604rx batch; learned-Δt vs 
 T_END = 1e-9
 N_ZONES = 4096
 WORKLOAD = "4096 zones x 150sp/1604rx, T9/rho profiles, t 1e-12 -> 1e-9 s"
+# the uneven-size batch: 2048 zones, 1:2:1, the chain over its own interval
+MIXED_ZONES = 2048
+MIXED_T_END = {"chain16_48": 1e-2, "net150_1604": 1e-9, "net365_4400": 1e-9}
 
 
 def _args():
@@ -37,13 +47,19 @@ def _args():
     ap.add_argument("--steps", type=int, default=5)
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
-    ap.add_argument("--form", default="mixed", choices=["mixed", "fp64"])
+    ap.add_argument("--form", default="mixed", choices=["mixed", "mixed_fp64", "fp64"])
     ap.add_argument("--zones", type=int, default=N_ZONES)
     ap.add_argument("--t-end", type=float, default=T_END, help="integration end time (s)")
+    ap.add_argument("--strong", action="store_true",
+                    help="under torchrun: split one batch of --zones zones over the ranks, balanced by predicted "
+                         "cost (strong scaling), instead of --zones zones per rank (weak scaling)")
     ap.add_argument("--no-cpu", action="store_true", help="skip the CPU baselines")
     ap.add_argument("--no-forms", action="store_true", help="skip the FP64 and learned-dt side measurements")
     ap.add_argument("--tpz", type=int, default=0)
     ap.add_argument("--tpc", type=int, default=0)
+    ap.add_argument("--mlp-train", action="store_true",
+                    help="instead of the batch benchmark: time the learned network's training kernels alone "
+                         "(fused forward + backward per 64-row tile, gradient reduction, Adam) and print that line")
     ap.add_argument("--sweep", action="store_true",
                     help="instead of the batch benchmark: time one integration step of a single network "
                          "against its size (GPU, CPU oracle, CPU backward Euler) and print that table")
@@ -310,34 +326,126 @@ def single_zone_configs():
     return out
 
 
-def _timed_form(kn, g, dz, stream, opts, reps=2):
-    """One warm-up and `reps` timed batches of a form; returns (ms/batch, stats)."""
+def _sm_clock_hz(clk):
+    return (clk.get("sm_mhz") or 2070.0) * 1e6
+
+
+def timed_batches(kn, nets, set_zones, opts, steps, warmup, stream, flush, zone_ns=None, barrier=None):
+    """`warmup` untimed batches, then `steps` timed ones.  Each timed batch:
+    the L2 flushed (untimed), then CUDA events on the launching stream around
+    the zone upload and the integration.  nvidia-smi clocks are sampled
+    during the timed batches.  zone_ns: a device [zones][2] int64 tensor that
+    receives the per-zone fetch and write-back times of every batch (the last
+    one is read back)."""
     import torch
-    g.set_zones(dz, stream)
-    kn.integrate_batch([g], opts, stream)
+    o = kn.Opts(**{**opts.__dict__, "zone_ns": zone_ns.data_ptr() if zone_ns is not None else 0})
+    for _ in range(warmup):
+        set_zones()
+        kn.integrate_batch(nets, o, stream)
     torch.cuda.synchronize()
-    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
-    ms = 0.0
-    for _ in range(reps):
-        g.set_zones(dz, stream)
-        e0.record(stream)
-        kn.integrate_batch([g], opts, stream)
-        e1.record(stream)
-        torch.cuda.synchronize()
-        ms += e0.elapsed_time(e1)
-    return ms / reps, kn.batch_stats([g], stream)
+    ev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True),
+           torch.cuda.Event(enable_timing=True)) for _ in range(steps)]
+    clocks = ClockSampler(torch.cuda.current_device())
+    clocks.start()
+    if barrier:
+        barrier()
+    torch.cuda.synchronize()
+    for i in range(steps):
+        flush.zero_()
+        ev[i][0].record(stream)
+        set_zones()
+        ev[i][1].record(stream)
+        kn.integrate_batch(nets, o, stream)
+        ev[i][2].record(stream)
+    torch.cuda.synchronize()
+    if barrier:
+        barrier()
+    clk = clocks.stop()
+    return {"step_ms": [a.elapsed_time(c) for a, b, c in ev], "kernel_ms": [b.elapsed_time(c) for a, b, c in ev],
+            "clocks": clk, "stats": kn.batch_stats(nets, stream),
+            "zone_ns": zone_ns.cpu().numpy() if zone_ns is not None else None}
 
 
-def other_forms(kn, g, net, zones, dz, stream, mixed_steps, mixed_ms):
-    """Side measurements on the same batch: the plain FP64 form and the mixed
-    form with the learned dt proposal (network trained here, untimed, on
-    records the integrator generates from training zones), each with its end-
-    state error against an oracle run at 10x tighter tolerances on 8 zones."""
+def tail_stats(zone_ns, steps, groups):
+    """From the per-zone timer stamps of one batch: the batch span, when the
+    work queue drained (the last fetch), the time after that (the tail), the
+    spread of zone finish times, the longest zone, and the mean occupancy of
+    the zone groups."""
+    ns = zone_ns.astype(np.float64)
+    t0 = ns[:, 0].min()
+    fetch = (ns[:, 0] - t0) / 1e6
+    end = (ns[:, 1] - t0) / 1e6
+    dur = end - fetch
+    i = int(np.argmax(dur))
+    span = float(end.max())
+    return {"span_ms": span, "queue_drained_ms": float(fetch.max()), "tail_ms": float(span - fetch.max()),
+            "finish_ms_p50_p90_p99_max": [float(np.percentile(end, q)) for q in (50, 90, 99, 100)],
+            "longest_zone": {"ms": float(dur[i]), "accepted_steps": int(steps[i]), "fetched_at_ms": float(fetch[i]),
+                             "us_per_step": float(dur[i] * 1e3 / max(1, steps[i]))},
+            "group_occupancy": float(dur.sum() / (groups * span)) if groups else None}
+
+
+def _mean(x):
+    return float(np.mean(x))
+
+
+def smem_roofline(parts, kms, clk, n_sms):
+    """Shared-memory roofline of the FP32-flux forms: the measurement plan's
+    bytes per accepted zone-step (algorithmic_smem_bytes, FP32 widths) over
+    the kernel time, against 128 B/clk/SM x SMs x the sampled SM clock.
+    parts: [(network, accepted steps, rejects)]."""
+    peak = 128.0 * n_sms * _sm_clock_hz(clk) / 1e9
+    b = sum(algorithmic_smem_bytes(n, st) for n, st, rj in parts)
+    bf = sum(full_smem_bytes(n, st, rj) for n, st, rj in parts)
+    return {"bound": "alu", "resource": "shared-memory bandwidth (SM-local)", "unit": "GB/s",
+            "kernel": "integrate_kernel", "achieved": b / (kms / 1e3) / 1e9, "peak": peak,
+            "frac": b / (kms / 1e3) / 1e9 / peak,
+            "peak_source": "derived: 128 B/clk/SM x SMs x sampled SM clock",
+            "algorithmic_smem_bytes_per_launch": b,
+            "algorithmic_unit": "per accepted zone-step: 4 S_r + 4 (S_r + R) + 2 (S_r + S_p) + 4 S_p bytes",
+            "full_count_smem_bytes_per_launch": bf, "full_count_frac": bf / (kms / 1e3) / 1e9 / peak,
+            "kernel_ms": kms}
+
+
+def fp64_roofline(flops, kms, fp64_peak, what):
+    return {"bound": "alu", "resource": "FP64 pipe", "unit": "TFLOP/s", "kernel": "integrate_kernel",
+            "achieved": flops / (kms / 1e3) / 1e12, "peak": fp64_peak, "frac": flops / (kms / 1e3) / 1e12 / fp64_peak,
+            "peak_source": "measured FP64 DFMA throughput (kn_measure_fp64_peak)",
+            "algorithmic_fp64_flops_per_launch": flops, "algorithmic_unit": what, "kernel_ms": kms,
+            "nominal_fp64_tflops": 1.25}
+
+
+def update_fp64_flops(net, attempts):
+    """FP64 operations of the kappa-switched update, the conservation sum and
+    the relative test: 11 per species per attempt (as in algorithmic_flops)."""
+    return float(attempts * 11 * net.n_species)
+
+
+def _form_line(tb, nets, zones_total, roof, extra=None):
+    st = tb["stats"]
+    kms = _mean(tb["kernel_ms"])
+    out = {"zone_steps_per_s": st["steps"] / (kms / 1e3), "zones_per_s": st["zones_ok"] / (kms / 1e3),
+           "ms_per_batch": _mean(tb["step_ms"]), "kernel_ms": kms, "kernel_ms_all": tb["kernel_ms"],
+           "accepted_steps": st["steps"], "rejects": st["rejects"], "zones": zones_total,
+           "zones_ok": st["zones_ok"], "clocks": tb["clocks"], "roofline": roof}
+    if extra:
+        out.update(extra)
+    return out
+
+
+def other_forms(kn, g, net, zones, dz, stream, flush, mixed_line, args):
+    """Every other form on the same batch, timed like the headline (3 warm-up
+    and 3 timed batches; the FP64 form, at ~10 s a batch, 1 + 2), each with
+    its roofline and its end-state error against an oracle run at 10x
+    tighter tolerances on 8 zones; then the perfect-proposal run, the
+    uneven-size batch and the learned network's training kernels."""
     import torch
     import oracle
-    from kn_inputs import chain_network, profile_zones
+    from kn_inputs import chain_network, net365, profile_zones, mixed_assignment
     from paper_1409_5826_gb300 import learned
     out = {}
+    n_sms = _n_sms()
+    fp64_peak = kn.measure_fp64_peak(stream)
     pick = np.linspace(0, zones.n_zones - 1, 8).astype(int)
     tight = oracle.Oracle(net).integrate_batch(zones.subset(pick), oracle.OracleOpts(eps_r=0.005, eps_c=1e-7),
                                                threads=os.cpu_count() or 1)
@@ -350,47 +458,191 @@ def other_forms(kn, g, net, zones, dz, stream, mixed_steps, mixed_ms):
             e.append(np.median(np.abs(Y[i][m] - tight["Y"][a][m]) / tight["Y"][a][m]))
         return float(np.median(e))
 
-    ms, st = _timed_form(kn, g, dz, stream, kn.Opts(precision=kn.PREC_MIXED, use_graph=1), reps=1)
-    out["mixed"] = {"ms_per_batch": ms, "zone_steps_per_s": st["steps"] / (ms / 1e3),
-                    "zones_per_s": st["zones_ok"] / (ms / 1e3), "steps": st["steps"], "rejects": st["rejects"],
-                    "median_rel_err_vs_tight_oracle": err()}
-    # the mixed form with the FP64 update: FP32 rates, fluxes and Kahan
+    def set_main():
+        g.set_zones(dz, stream)
+
+    out["mixed"] = {"median_rel_err_vs_tight_oracle": err(), "see": "the headline value and roofline"}
+    # the split the measurement plan names: FP32 rates, fluxes and Kahan
     # gathers; FP64 update, conservation sum and test
     g.set_zones(dz, stream)
-    kn.autotune([g], kn.Opts(precision=kn.PREC_MIXED_FP64), max_steps=3000, stream=stream)
-    ms, st = _timed_form(kn, g, dz, stream, kn.Opts(precision=kn.PREC_MIXED_FP64, use_graph=1), reps=1)
-    out["mixed_fp64_update"] = {"ms_per_batch": ms, "zone_steps_per_s": st["steps"] / (ms / 1e3),
-                                "zones_per_s": st["zones_ok"] / (ms / 1e3), "steps": st["steps"],
-                                "rejects": st["rejects"], "median_rel_err_vs_tight_oracle": err()}
+    tuned = kn.autotune([g], kn.Opts(precision=kn.PREC_MIXED_FP64), max_steps=3000, stream=stream)
+    tb = timed_batches(kn, [g], set_main, kn.Opts(precision=kn.PREC_MIXED_FP64, use_graph=1), 3, 3, stream, flush)
+    kms = _mean(tb["kernel_ms"])
+    st = tb["stats"]
+    roof = fp64_roofline(update_fp64_flops(net, st["steps"] + st["rejects"]), kms, fp64_peak,
+                         "11 FP64 operations per species per attempt (update, conservation sum, test)")
+    roof["smem"] = smem_roofline([(net, st["steps"], st["rejects"])], kms, tb["clocks"], n_sms)
+    out["mixed_fp64_update"] = _form_line(tb, [g], zones.n_zones, roof,
+                                          {"median_rel_err_vs_tight_oracle": err(), "tiling": tuned})
+    # every step in FP64
     g.set_zones(dz, stream)
-    kn.autotune([g], kn.Opts(precision=kn.PREC_FP64), max_steps=100, stream=stream)
-    ms, st = _timed_form(kn, g, dz, stream, kn.Opts(precision=kn.PREC_FP64, use_graph=1), reps=1)
-    out["fp64"] = {"ms_per_batch": ms, "zone_steps_per_s": st["steps"] / (ms / 1e3),
-                   "zones_per_s": st["zones_ok"] / (ms / 1e3), "steps": st["steps"], "rejects": st["rejects"],
-                   "median_rel_err_vs_tight_oracle": err()}
+    tuned = kn.autotune([g], kn.Opts(precision=kn.PREC_FP64), max_steps=100, stream=stream)
+    tb = timed_batches(kn, [g], set_main, kn.Opts(precision=kn.PREC_FP64, use_graph=1), 2, 1, stream, flush)
+    st = tb["stats"]
+    roof = fp64_roofline(algorithmic_flops(net, st["steps"], st["rejects"]), _mean(tb["kernel_ms"]), fp64_peak,
+                         "rates 5 R + fluxes 1/3/7 per 1/2/3-body reaction + gathers S_r + S_p per accepted step, "
+                         "11 N per attempt")
+    out["fp64"] = _form_line(tb, [g], zones.n_zones, roof, {"median_rel_err_vs_tight_oracle": err(), "tiling": tuned})
+    # the learned proposal: records from training zones, training on the GPU,
+    # then the batch with the network proposing and the plain test judging
     t0 = time.perf_counter()
     jobs = [(net, profile_zones(net, 128, base_seed=500_000, t_end=T_END)),
             (chain_network(), profile_zones(chain_network(), 32, base_seed=600_000, t_end=1e-2))]
     feat, lab = learned.generate_records(jobs, 2_000_000, stream=stream)
     rec_s = time.perf_counter() - t0
     t0 = time.perf_counter()
-    mlp, hist = learned.train_network(feat, lab, epochs=4, batch=4096, lr=1e-3, stream=stream)
+    mlp, hist, train_kernel_s = learned.train_network(feat, lab, epochs=4, batch=4096, lr=1e-3, stream=stream,
+                                                      time_kernels=True)
     torch.cuda.synchronize()
     train_s = time.perf_counter() - t0
     g.set_zones(dz, stream)
-    kn.autotune([g], kn.Opts(precision=kn.PREC_MIXED, mlp=mlp), max_steps=300, stream=stream)
-    ms, st = _timed_form(kn, g, dz, stream, kn.Opts(precision=kn.PREC_MIXED, mlp=mlp, use_graph=1), reps=1)
-    out["mixed_learned"] = {"ms_per_batch": ms, "zone_steps_per_s": st["steps"] / (ms / 1e3),
-                            "zones_per_s": st["zones_ok"] / (ms / 1e3), "steps": st["steps"],
-                            "rejects": st["rejects"], "proposals_used": st["proposals_used"],
-                            "median_rel_err_vs_tight_oracle": err(),
-                            "records": int(feat.shape[0]), "record_gen_s": rec_s, "train_s": train_s,
-                            "train_loss_first_last": [hist[0], hist[-1]]}
-    out["learned_vs_plain_mixed_zones_per_s"] = out["mixed_learned"]["zones_per_s"] / out["mixed"]["zones_per_s"]
+    tuned = kn.autotune([g], kn.Opts(precision=kn.PREC_MIXED, mlp=mlp), max_steps=300, stream=stream)
+    tb = timed_batches(kn, [g], set_main, kn.Opts(precision=kn.PREC_MIXED, mlp=mlp, use_graph=1), 3, 3, stream, flush)
+    st = tb["stats"]
+    kms = _mean(tb["kernel_ms"])
+    roof = smem_roofline([(net, st["steps"], st["rejects"])], kms, tb["clocks"], n_sms)
+    # the network evaluation on CUDA cores: 2 (64 128 + 128 128 + 128) flops
+    # per proposal, one proposal per state reached by an accepted step
+    mlp_flops = 2.0 * (64 * 128 + 128 * 128 + 128) * (st["steps"] - zones.n_zones)
+    fp32_peak = 2.0 * 128 * n_sms * _sm_clock_hz(tb["clocks"]) / 1e12
+    roof["mlp_inference"] = {"unit": "TFLOP/s", "flops_per_launch": mlp_flops,
+                             "achieved_over_kernel_time": mlp_flops / (kms / 1e3) / 1e12, "peak": fp32_peak,
+                             "peak_source": "derived: 128 FP32 FMA lanes/clk/SM x 2 x SMs x sampled clock"}
+    out["mixed_learned"] = _form_line(tb, [g], zones.n_zones, roof, {
+        "proposals_used": st["proposals_used"], "median_rel_err_vs_tight_oracle": err(), "tiling": tuned,
+        "records": int(feat.shape[0]), "record_gen_s": rec_s, "train_s": train_s,
+        "train_kernel_s": train_kernel_s, "train_loss_first_last": [hist[0], hist[-1]]})
+    out["learned_vs_plain_mixed_zones_per_s"] = out["mixed_learned"]["zones_per_s"] / mixed_line["zones_per_s"]
     out["learned_mixed_vs_plain_fp64_zones_per_s"] = out["mixed_learned"]["zones_per_s"] / out["fp64"]["zones_per_s"]
-    out["note"] = "side measurements: 1 warm-up + 1 timed batch each, same 4096-zone batch"
+    del feat, lab
+    # the learned network's training kernels alone: fused forward + backward
+    # and the Adam step on batches of 4096 records, back to back
+    out["mlp_training_kernels"] = mlp_training_roofline(kn, mlp, stream)
     mlp.close()
+    # the perfect proposal: every state reached by an accepted step tries the
+    # step the records' label names (the largest grid step before the first
+    # that fails), clipped like a learned proposal; what it saves bounds what
+    # any learned proposal of this form can save
+    out["perfect_proposal_ceiling"] = perfect_proposal(kn, g, dz, stream)
+    # the uneven-size batch: 16/48 : 150/1604 : 365/4400 = 1:2:1 in one launch
+    out["uneven_sizes"] = uneven_sizes(kn, stream, flush, n_sms, args)
+    out["note"] = ("every form: warm-up batches, then timed batches with CUDA events on the launching stream, "
+                   "L2 flushed between batches, clocks sampled; errors against an oracle run at eps_r 0.005, "
+                   "eps_c 1e-7 on 8 zones of the batch")
     return out
+
+
+def mlp_training_roofline(kn, mlp, stream, B=4096, batches=200):
+    """CUDA-event time of `batches` training steps (kn_mlp_backward: the fused
+    forward + backward tile kernel and the partial-gradient reduction; then
+    kn_mlp_adam) on random records, against the BF16 tensor peak."""
+    import torch
+    dev = torch.device("cuda", torch.cuda.current_device())
+    gen = torch.Generator(device=dev)
+    gen.manual_seed(3)
+    feat = torch.randn((B, 64), generator=gen, device=dev, dtype=torch.float32)
+    lab = torch.randn(B, generator=gen, device=dev, dtype=torch.float32)
+    loss = torch.zeros(1, dtype=torch.float32, device=dev)
+    for _ in range(5):
+        mlp.backward(feat, lab, loss, stream)
+        mlp.adam(1e-6, stream=stream)
+    torch.cuda.synchronize()
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    e0.record(stream)
+    for _ in range(batches):
+        mlp.backward(feat, lab, loss, stream)
+        mlp.adam(1e-6, stream=stream)
+    e1.record(stream)
+    torch.cuda.synchronize()
+    us = e0.elapsed_time(e1) * 1e3 / batches
+    # GEMM flops per step: forward 2 B (64 128 + 128 128); backward dZ1 2 B 128 128,
+    # dW2 2 B 128 128, dW1 2 B 64 128
+    flops = 2.0 * B * (64 * 128 + 128 * 128) + 2.0 * B * (128 * 128 + 128 * 128 + 64 * 128)
+    peaks, src = _peaks()
+    return {"batch": B, "us_per_training_step": us, "gemm_flops_per_step": flops,
+            "achieved_tflops": flops / (us / 1e6) / 1e12, "peak_tflops": peaks["bf16_tflops"],
+            "frac": flops / (us / 1e6) / 1e12 / peaks["bf16_tflops"],
+            "peak_source": f"MEASURED_PEAKS.json bf16_tflops ({src}), dense BF16", "bound": "tensor",
+            "launches_per_step": 3}
+
+
+def perfect_proposal(kn, g, dz, stream):
+    """Accepted steps and attempts of the plain controller and of the perfect
+    proposal on the bench batch (mixed form; untimed: the label search runs
+    the update up to 25 times per state)."""
+    import torch
+    dev = torch.device("cuda", torch.cuda.current_device())
+    feat = torch.empty((1, 64), dtype=torch.float32, device=dev)
+    lab = torch.empty(1, dtype=torch.float32, device=dev)
+    res = {}
+    for follow in (0, 1):
+        cnt = torch.zeros(1, dtype=torch.int64, device=dev)
+        g.set_zones(dz, stream)
+        t0 = time.perf_counter()
+        kn.integrate_batch([g], kn.Opts(precision=kn.PREC_MIXED, record_features=feat.data_ptr(),
+                                        record_labels=lab.data_ptr(), record_capacity=0,
+                                        record_count=cnt.data_ptr(), follow_label=follow), stream)
+        torch.cuda.synchronize()
+        st = kn.batch_stats([g], stream)
+        res["perfect" if follow else "plain"] = {"accepted_steps": st["steps"], "rejects": st["rejects"],
+                                                 "attempts": st["steps"] + st["rejects"],
+                                                 "proposals_used": st["proposals_used"],
+                                                 "wall_s": time.perf_counter() - t0}
+    p, q = res["plain"], res["perfect"]
+    res["steps_ratio"] = q["accepted_steps"] / p["accepted_steps"]
+    res["attempts_ratio"] = q["attempts"] / p["attempts"]
+    res["note"] = ("perfect: at every state the label's step (largest grid step dt_prev 2^(k/4) before the first "
+                   "that fails), clipped to [dt_plain, 16 dt_plain]; attempts_ratio is the most a learned "
+                   "proposal could save")
+    return res
+
+
+def uneven_sizes(kn, stream, flush, n_sms, args):
+    """2048 zones of the 16/48, 150/1604 and 365/4400 networks in the ratio
+    1:2:1 (shuffled assignment, config-3 profiles; the chain over 1e-12 ->
+    1e-2 s, the others over 1e-12 -> 1e-9 s), all in one persistent launch
+    with the autotuned tiling."""
+    import torch
+    from kn_inputs import chain_network, mixed_assignment, net150, net365, profile_zones
+    nets = {"chain16_48": chain_network(), "net150_1604": net150(), "net365_4400": net365()}
+    lab = mixed_assignment(MIXED_ZONES, (1, 2, 1))
+    dev = torch.device("cuda", torch.cuda.current_device())
+    names = ("Y0", "T0", "rho0", "tau", "t_start", "t_end", "dt_trial")
+    gs, dzs, counts = [], [], {}
+    for k, (name, net) in enumerate(nets.items()):
+        idx = np.nonzero(lab == k)[0]
+        # zone z of the batch draws its profile from seed 1000 + z
+        z = profile_zones(net, MIXED_ZONES, t_end=MIXED_T_END[name]).subset(idx)
+        g = kn.Network(net)
+        d = {n: torch.from_numpy(np.ascontiguousarray(getattr(z, n))).to(dev) for n in names}
+        gs.append(g)
+        dzs.append(d)
+        counts[name] = int(len(idx))
+
+    def set_all():
+        for g, d in zip(gs, dzs):
+            g.set_zones(d, stream)
+
+    set_all()
+    tuned = kn.autotune(gs, kn.Opts(precision=kn.PREC_MIXED), max_steps=0, stream=stream)
+    zns = torch.zeros((MIXED_ZONES, 2), dtype=torch.int64, device=dev)
+    tb = timed_batches(kn, gs, set_all, kn.Opts(precision=kn.PREC_MIXED, use_graph=1), 3, 3, stream, flush, zns)
+    kms = _mean(tb["kernel_ms"])
+    per, parts, steps_all = {}, [], []
+    for (name, net), g in zip(nets.items(), gs):
+        st = kn.batch_stats([g], stream)
+        r = g.get(stream)
+        steps_all.append(r["steps"])
+        per[name] = {"zones": counts[name], "zones_ok": st["zones_ok"], "accepted_steps": st["steps"],
+                     "rejects": st["rejects"], "zones_per_s": st["zones_ok"] / (kms / 1e3),
+                     "zone_steps_per_s": st["steps"] / (kms / 1e3), "t_end": MIXED_T_END[name]}
+        parts.append((net, st["steps"], st["rejects"]))
+    roof = smem_roofline(parts, kms, tb["clocks"], n_sms)
+    line = _form_line(tb, gs, MIXED_ZONES, roof, {"per_network": per, "tiling": tuned})
+    line["tail"] = tail_stats(tb["zone_ns"], np.concatenate(steps_all), None)
+    for g in gs:
+        g.close()
+    return line
 
 
 def main():
@@ -409,6 +661,17 @@ def main():
         if rank == 0:
             size_sweep(args)
         return
+    if args.mlp_train:
+        if rank == 0:
+            import torch
+            from paper_1409_5826_gb300 import build, kn, learned
+            build.build()
+            mlp = kn.MLP()
+            mlp.set_params(learned.init_params(0), np.zeros(64, np.float32), np.ones(64, np.float32))
+            print(json.dumps({"mlp_training_kernels": mlp_training_roofline(kn, mlp, torch.cuda.current_stream(),
+                                                                            batches=args.steps)}), flush=True)
+            mlp.close()
+        return
     import torch
     torch.cuda.set_device(local)
     if world > 1:
@@ -422,15 +685,20 @@ def main():
         dist.barrier()
     build.build()
     net = net150()
-    # weak scaling: each rank integrates its own slice of the global batch
     from paper_1409_5826_gb300 import shard
-    zones = profile_zones(net, args.zones, base_seed=shard.zone_seed_base(rank, world, args.zones),
-                          t_end=args.t_end)
+    if args.strong:
+        # strong scaling: one batch, split over the ranks balanced by predicted cost
+        whole = profile_zones(net, args.zones, t_end=args.t_end)
+        zones = whole.subset(shard.balanced_partition(shard.cost_key(net, whole), world)[rank])
+    else:
+        # weak scaling: each rank integrates its own slice of the global batch
+        zones = profile_zones(net, args.zones, base_seed=shard.zone_seed_base(rank, world, args.zones),
+                              t_end=args.t_end)
     dev = torch.device("cuda", local)
     names = ("Y0", "T0", "rho0", "tau", "t_start", "t_end", "dt_trial")
     dz = {k: torch.from_numpy(np.ascontiguousarray(getattr(zones, k))).to(dev) for k in names}
     g = kn.Network(net)
-    prec = kn.PREC_MIXED if args.form == "mixed" else kn.PREC_FP64
+    prec = {"mixed": kn.PREC_MIXED, "mixed_fp64": kn.PREC_MIXED_FP64, "fp64": kn.PREC_FP64}[args.form]
     stream = torch.cuda.current_stream()
     tuned = None
     if not (args.tpz or args.tpc):
@@ -441,38 +709,18 @@ def main():
     opts = kn.Opts(precision=prec, use_graph=1, threads_per_zone=args.tpz, threads_per_cta=args.tpc)
     flush = torch.empty(256 * 1024 * 1024 // 4, dtype=torch.float32, device=dev)  # > L2 (129 MB)
 
-    def step():
+    def set_main():
         g.set_zones(dz, stream)
-        kn.integrate_batch([g], opts, stream)
 
-    for _ in range(max(3, args.warmup)):
-        step()
-    torch.cuda.synchronize()
-    stats = kn.batch_stats([g], stream)
-    ev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True),
-           torch.cuda.Event(enable_timing=True)) for _ in range(args.steps)]
-    clocks = ClockSampler(local)
-    clocks.start()
-    if world > 1:
-        dist.barrier()
-    torch.cuda.synchronize()
-    for i in range(args.steps):
-        flush.zero_()  # untimed: L2 flushed between timed steps
-        ev[i][0].record(stream)
-        g.set_zones(dz, stream)
-        ev[i][1].record(stream)
-        kn.integrate_batch([g], opts, stream)
-        ev[i][2].record(stream)
-    torch.cuda.synchronize()
-    if world > 1:
-        dist.barrier()
-    clk = clocks.stop()
-    step_ms = [a.elapsed_time(c) for a, b, c in ev]
-    kern_ms = [b.elapsed_time(c) for a, b, c in ev]
-    ms = float(np.sum(step_ms))
-    st = kn.batch_stats([g], stream)
+    zns = torch.zeros((zones.n_zones, 2), dtype=torch.int64, device=dev)
+    tb = timed_batches(kn, [g], set_main, opts, args.steps, max(3, args.warmup), stream, flush, zns,
+                       barrier=dist.barrier if world > 1 else None)
+    clk = tb["clocks"]
+    ms = float(np.sum(tb["step_ms"]))
+    st = tb["stats"]
     steps_per_batch = st["steps"]
     zones_ok = st["zones_ok"]
+    zone_steps = g.get(stream)["steps"]
     ms, steps_all, zones_all = shard.aggregate(ms, steps_per_batch, zones_ok, device=dev)
     value = steps_all * args.steps / (ms / 1e3)
 
@@ -503,61 +751,57 @@ def main():
             dist.barrier()
             dist.destroy_process_group()
         return
-    kms = float(np.mean(kern_ms))
+    kms = _mean(tb["kernel_ms"])
+    n_sms = _n_sms()
+    if args.form == "fp64":
+        roof = fp64_roofline(algorithmic_flops(net, st["steps"], st["rejects"]), kms, kn.measure_fp64_peak(stream),
+                             "rates 5 R + fluxes 1/3/7 per 1/2/3-body reaction + gathers S_r + S_p per accepted "
+                             "step, 11 N per attempt")
+    else:
+        # SM-local bound: shared-memory bandwidth, 32 banks x 4 B per clock per
+        # SM at the SM clock sampled during the timed steps
+        roof = smem_roofline([(net, st["steps"], st["rejects"])], kms, clk, n_sms)
     # DRAM traffic of the integrator from the committed ncu capture of this
     # kernel (small case, mixed form), scaled to this launch by zone count
     # (each zone's state is read once per launch); null when the kernel's
-    # sources changed since the capture or for the FP64 form
+    # sources changed since the capture, or for another form
     prof = _profile_line("integrate_kernel_mixed_1216x150_full.md")
     traffic = None
     if prof and args.form == "mixed" and prof[2] == kernel_sources_sha256():
         traffic = prof[0] * args.zones / prof[1]
-    if args.form == "mixed":
-        # SM-local bound: shared-memory bandwidth, 32 banks x 4 B per clock per
-        # SM at the SM clock sampled during the timed steps
-        sm_hz = (clk.get("sm_mhz") or 2070.0) * 1e6
-        peak = 128.0 * _n_sms() * sm_hz / 1e9
-        b = algorithmic_smem_bytes(net, st["steps"])
-        bf = full_smem_bytes(net, st["steps"], st["rejects"])
-        roof = {"bound": "alu", "resource": "shared-memory bandwidth (SM-local)", "unit": "GB/s",
-                "kernel": "integrate_kernel", "achieved": b / (kms / 1e3) / 1e9, "peak": peak,
-                "peak_source": "derived: 128 B/clk/SM x SMs x sampled SM clock",
-                "traffic": traffic,
-                "traffic_source": "profiles/integrate_kernel_mixed_1216x150_full.md, scaled by zones"
-                if traffic else None,
-                "algorithmic_smem_bytes_per_launch": b,
-                "algorithmic_unit": "per accepted zone-step: 4 S_r + 4 (S_r + R) + 2 (S_r + S_p) + 4 S_p bytes",
-                "full_count_smem_bytes_per_launch": bf, "full_count_frac": bf / (kms / 1e3) / 1e9 / peak,
-                "kernel_ms": kms}
-    else:
-        # FP64 pipe bound: the peak is the device's DFMA throughput measured
-        # here (the peaks file has no FP64 figure); nominal 1.25 TFLOP/s
-        f64 = algorithmic_flops(net, st["steps"], st["rejects"])
-        roof = {"bound": "alu", "resource": "FP64 pipe", "unit": "TFLOP/s", "kernel": "integrate_kernel",
-                "achieved": f64 / (kms / 1e3) / 1e12, "peak": kn.measure_fp64_peak(stream),
-                "peak_source": "measured FP64 DFMA throughput (kn_measure_fp64_peak)", "traffic": None,
-                "algorithmic_fp64_flops_per_launch": f64, "kernel_ms": kms, "nominal_fp64_tflops": 1.25}
-    roof["frac"] = roof["achieved"] / roof["peak"]
+    roof["traffic"] = traffic
+    roof["traffic_source"] = ("ncu capture of the mixed-form kernel on 1216 zones (committed summary), "
+                              "scaled by zones") if traffic else None
     if traffic:
         # context: the DRAM side is far from its bound
         peaks, src = _peaks()
         roof["dram_gbs"] = traffic / (kms / 1e3) / 1e9
         roof["dram_frac_of_hbm"] = roof["dram_gbs"] / peaks["hbm_gbs"]
         roof["hbm_peak_source"] = f"MEASURED_PEAKS.json hbm_gbs ({src})"
+    groups = None
+    if tuned:
+        groups = n_sms * (tuned["threads_per_cta"] // tuned["threads_per_zone"])
+    elif args.tpz and args.tpc:
+        groups = n_sms * (args.tpc // args.tpz)
+    dtype = {"mixed": "f32 (float-float state)", "mixed_fp64": "f32 fluxes, f64 update", "fp64": "f64"}[args.form]
     line = {"metric": METRIC, "value": value, "unit": "zone-steps/s", "n_gpus": world, "steps": args.steps,
             "warmup": max(3, args.warmup), "ms_per_step": ms / args.steps, "higher_is_better": True,
-            "scaling": "weak", "vs_baseline": None, "dtype": "f32 (float-float state)" if args.form == "mixed" else "f64",
+            "scaling": "strong" if args.strong else "weak", "vs_baseline": None, "dtype": dtype,
             "data": "synthetic", "zones_per_s": zones_all * args.steps / (ms / 1e3),
             "config": {"workload": WORKLOAD if (args.zones, args.t_end) == (N_ZONES, T_END) else
                        f"{args.zones} zones x 150sp/1604rx, T9/rho profiles, t 1e-12 -> {args.t_end:g} s",
-                       "zones_per_gpu": args.zones, "n_species": 150, "n_reactions": 1604,
+                       "zones_per_gpu": zones.n_zones, "n_species": 150, "n_reactions": 1604,
                        "form": args.form, "l2": "flushed between timed steps (256 MB write)",
                        "accepted_steps_per_batch": int(steps_per_batch), "rejects_per_batch": int(st["rejects"]),
                        "zones_ok": int(zones_ok), "parallelism": f"zones sharded, {world} GPU(s)",
                        "tiling": tuned if tuned else {"threads_per_zone": args.tpz, "threads_per_cta": args.tpc}},
-            "clocks": clk, "e2e": e2e, "gpu_launches": 3 * args.steps, "roofline": roof}
-    if not args.no_forms:
-        line["forms"] = other_forms(kn, g, net, zones, dz, stream, st["steps"], kms)
+            "clocks": clk, "e2e": e2e, "gpu_launches": 3 * args.steps, "roofline": roof,
+            "tail": tail_stats(tb["zone_ns"], zone_steps, groups),
+            "paper_context": ("the paper estimates ~100 150-isotope networks integrated on one Kepler GPU "
+                              "(Tesla K20X class) in the time an implicit CPU code integrates one (abstract, Sec. 9)")}
+    if not args.no_forms and args.form == "mixed":
+        line["forms"] = other_forms(kn, g, net, zones, dz, stream, flush,
+                                    {"zones_per_s": zones_ok / (kms / 1e3)}, args)
         line["single_zone"] = single_zone_configs()
     if not args.no_cpu:
         exp, be = cpu_baselines(net, zones)

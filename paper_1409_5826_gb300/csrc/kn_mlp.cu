@@ -3,10 +3,16 @@
 // trained with Adam (Kingma & Ba).  The paper has no learned component; this
 // is the library's addition on top of the Sec. 4 timestep controller.
 //
-// Training GEMMs run on the tensor cores with mma.sync.m16n8k16 (BF16 inputs,
-// FP32 accumulate).  The batch GEMMs here are tiny (a few hundred MFLOP per
-// training step), so one warp per 16x8 output tile with strided fragment
-// loads is enough; every fragment load is bounds-checked, so any M, N, K work.
+// Training: one kernel per batch does the forward and backward pass of a
+// 64-row tile per CTA entirely in shared memory -- weights, inputs, hidden
+// activations and their gradients staged in 16-byte padded rows, every GEMM
+// on the tensor cores with ldmatrix and mma.sync.m16n8k16 (BF16 operands,
+// FP32 accumulation) -- and writes the tile's partial weight gradients; a
+// second kernel adds the tiles in a fixed order, then Adam updates the FP32
+// master weights.  Per batch of 4096 rows the three GEMM layers hold about
+// 0.6 GFLOP spread over 64 CTAs, so the tiles are latency-bound; the fusion
+// removes the activations' round trips through global memory and all but
+// three launches per step.
 #include <cuda_bf16.h>
 
 #include <cmath>
@@ -32,10 +38,10 @@ struct kn_mlp {
     float* Av = nullptr;  // Adam second moments
     bf16* Wb = nullptr;   // BF16 copies of W1 then W2 (same layouts as the master)
     float* norm = nullptr;  // mu [64], inv_sigma [64]
-    // activations for a batch of up to cap rows
-    int cap = 0;
-    bf16 *X = nullptr, *H1 = nullptr, *H2 = nullptr, *dZ2 = nullptr, *dZ1 = nullptr;
-    float *out = nullptr, *dout = nullptr;
+    // per-tile partial gradients [tiles][kPartStride] and squared errors [tiles], for up to cap_tiles tiles
+    int cap_tiles = 0;
+    float* part = nullptr;
+    float* loss_part = nullptr;
     long long step = 0;
 };
 
@@ -46,125 +52,259 @@ constexpr int OFF_W1 = 0, OFF_B1 = OFF_W1 + NF * NH, OFF_W2 = OFF_B1 + NH, OFF_B
               OFF_W3 = OFF_B2 + NH, OFF_B3 = OFF_W3 + NH;
 static_assert(OFF_B3 + 1 == kMlpParams, "parameter layout");
 
-__device__ __forceinline__ uint32_t pack_bf16(bf16 lo, bf16 hi) {
-    return (uint32_t)__bfloat16_as_ushort(lo) | ((uint32_t)__bfloat16_as_ushort(hi) << 16);
+__device__ __forceinline__ uint32_t smem_addr(const void* p) { return (uint32_t)__cvta_generic_to_shared(p); }
+
+// ldmatrix: four 8x8 BF16 matrices; lane l gives the row address of matrix l / 8.
+__device__ __forceinline__ void ldsm_x4(uint32_t (&r)[4], uint32_t addr) {
+    asm volatile("ldmatrix.sync.aligned.m8n8.x4.shared.b16 {%0,%1,%2,%3}, [%4];\n"
+                 : "=r"(r[0]), "=r"(r[1]), "=r"(r[2]), "=r"(r[3])
+                 : "r"(addr));
+}
+__device__ __forceinline__ void ldsm_x4_t(uint32_t (&r)[4], uint32_t addr) {
+    asm volatile("ldmatrix.sync.aligned.m8n8.x4.trans.shared.b16 {%0,%1,%2,%3}, [%4];\n"
+                 : "=r"(r[0]), "=r"(r[1]), "=r"(r[2]), "=r"(r[3])
+                 : "r"(addr));
+}
+// D += A (16x16, row) B (16x8, col), BF16 inputs, FP32 accumulation
+__device__ __forceinline__ void mma_bf16(float (&c)[4], const uint32_t (&a)[4], uint32_t b0, uint32_t b1) {
+    asm volatile(
+        "mma.sync.aligned.m16n8k16.row.col.f32.bf16.bf16.f32 {%0,%1,%2,%3}, {%4,%5,%6,%7}, {%8,%9}, "
+        "{%0,%1,%2,%3};\n"
+        : "+f"(c[0]), "+f"(c[1]), "+f"(c[2]), "+f"(c[3])
+        : "r"(a[0]), "r"(a[1]), "r"(a[2]), "r"(a[3]), "r"(b0), "r"(b1));
 }
 
-enum { EPI_F32 = 0, EPI_RELU_BF16 = 1, EPI_MASK_BF16 = 2 };
-
-// C[m][n] = sum_k A(m,k) B(k,n) (+ bias[n]); A(m,k) = A[m*sam + k*sak],
-// B(k,n) = B[k*sbk + n*sbn].  One warp per 16x8 tile of C.
-template <int EPI>
-__global__ void gemm_bf16(int M, int N, int K, const bf16* __restrict__ A, long sam, long sak,
-                          const bf16* __restrict__ B, long sbk, long sbn, const float* __restrict__ bias,
-                          void* C, long ldc, const bf16* __restrict__ mask, long ldm) {
-    const int warp = (blockIdx.x * blockDim.x + threadIdx.x) >> 5, lane = threadIdx.x & 31;
-    const int tiles_n = (N + 7) >> 3;
-    const int tm = warp / tiles_n, tn = warp - tm * tiles_n;
-    if (tm * 16 >= M) return;  // uniform across the warp
-    const int m0 = tm * 16, n0 = tn * 8, g = lane >> 2, t = lane & 3;
-    const bf16 z = __float2bfloat16(0.f);
-    auto lda = [&](int m, int k) { return (m < M && k < K) ? A[m * sam + k * sak] : z; };
-    auto ldb = [&](int k, int n) { return (k < K && n < N) ? B[k * sbk + n * sbn] : z; };
-    float c[4] = {0.f, 0.f, 0.f, 0.f};
+// Warp tile of C (16 rows from m0, 8*NT columns from n0) += A B over K, all
+// operands BF16 in shared memory with 16-byte padded rows (conflict-free
+// ldmatrix).  Operand storage:
+//   A_ROW: A is [M][K] (row m holds K values);  else A is stored [K][M].
+//   B_ROW: B is [K][N] (row k holds N values);  else B is stored [N][K].
+// Lane l addresses row (l & 7) of matrix l >> 3 of each ldmatrix.x4.
+template <int NT, bool A_ROW, bool B_ROW>
+__device__ __forceinline__ void warp_mma(float (&c)[NT][4], const bf16* A, int lda, int m0, const bf16* B, int ldb,
+                                         int n0, int K, int lane) {
+    const int r = lane & 7, q = lane >> 3;
+    const int lo8 = (q & 1) << 3, hi8 = (q & 2) << 2;  // matrix q: +8 on its first / second index
+#pragma unroll 2
     for (int k0 = 0; k0 < K; k0 += 16) {
-        uint32_t a[4], b[2];
-        a[0] = pack_bf16(lda(m0 + g, k0 + 2 * t), lda(m0 + g, k0 + 2 * t + 1));
-        a[1] = pack_bf16(lda(m0 + g + 8, k0 + 2 * t), lda(m0 + g + 8, k0 + 2 * t + 1));
-        a[2] = pack_bf16(lda(m0 + g, k0 + 2 * t + 8), lda(m0 + g, k0 + 2 * t + 9));
-        a[3] = pack_bf16(lda(m0 + g + 8, k0 + 2 * t + 8), lda(m0 + g + 8, k0 + 2 * t + 9));
-        b[0] = pack_bf16(ldb(k0 + 2 * t, n0 + g), ldb(k0 + 2 * t + 1, n0 + g));
-        b[1] = pack_bf16(ldb(k0 + 2 * t + 8, n0 + g), ldb(k0 + 2 * t + 9, n0 + g));
-        asm volatile(
-            "mma.sync.aligned.m16n8k16.row.col.f32.bf16.bf16.f32 {%0,%1,%2,%3}, {%4,%5,%6,%7}, {%8,%9}, "
-            "{%0,%1,%2,%3};\n"
-            : "+f"(c[0]), "+f"(c[1]), "+f"(c[2]), "+f"(c[3])
-            : "r"(a[0]), "r"(a[1]), "r"(a[2]), "r"(a[3]), "r"(b[0]), "r"(b[1]));
-    }
+        uint32_t a[4];
+        if (A_ROW)  // matrices (m, k): (0,0) (8,0) (0,8) (8,8)
+            ldsm_x4(a, smem_addr(A + (m0 + r + lo8) * lda + k0 + hi8));
+        else        // stored [k][m], transposed: (k, m) = (0,0) (0,8) (8,0) (8,8)
+            ldsm_x4_t(a, smem_addr(A + (k0 + r + hi8) * lda + m0 + lo8));
 #pragma unroll
-    for (int i = 0; i < 4; ++i) {
-        const int m = m0 + g + (i >> 1) * 8, n = n0 + 2 * t + (i & 1);
-        if (m >= M || n >= N) continue;
-        float v = c[i] + (bias ? bias[n] : 0.f);
-        if (EPI == EPI_F32) {
-            ((float*)C)[m * ldc + n] = v;
-        } else if (EPI == EPI_RELU_BF16) {
-            ((bf16*)C)[m * ldc + n] = __float2bfloat16(v > 0.f ? v : 0.f);
-        } else {
-            const float keep = __bfloat162float(mask[m * ldm + n]) > 0.f ? 1.f : 0.f;
-            ((bf16*)C)[m * ldc + n] = __float2bfloat16(v * keep);
+        for (int j = 0; j < NT; j += 2) {
+            uint32_t b[4];
+            if (B_ROW)  // stored [k][n], transposed: (k, n) = (0,0) (8,0) (0,8) (8,8)
+                ldsm_x4_t(b, smem_addr(B + (k0 + r + lo8) * ldb + n0 + 8 * j + hi8));
+            else        // stored [n][k]: (n, k) = (0,0) (0,8) (8,0) (8,8)
+                ldsm_x4(b, smem_addr(B + (n0 + 8 * j + r + hi8) * ldb + k0 + lo8));
+            mma_bf16(c[j], a, b[0], b[1]);
+            mma_bf16(c[j + 1], a, b[2], b[3]);
         }
     }
 }
 
-__global__ void prep_x(const float* __restrict__ f, int B, const float* __restrict__ norm, bf16* __restrict__ X) {
-    const int i = blockIdx.x * blockDim.x + threadIdx.x;
-    if (i < B * NF) {
-        const int k = i % NF;
-        X[i] = __float2bfloat16((f[i] - norm[k]) * norm[NF + k]);
+// One CTA per tile of kTileRows rows of the batch: the whole forward pass and,
+// with BWD, the backward pass of the mean squared error, every GEMM on the
+// tensor cores from shared memory.  Row-tile partial gradients (in the
+// parameter layout) and the tile's sum of squared errors go to global memory;
+// reduce_partials adds the tiles in a fixed order.
+constexpr int kTileRows = 64;
+// row stride of the per-tile partial gradients: the parameter count padded to
+// 16 bytes, so every tile's row keeps the float2 stores 8-byte aligned
+constexpr int kPartStride = (kMlpParams + 3) & ~3;
+constexpr int kTileThreads = 256;  // 8 warps
+constexpr int LDF = NF + 8, LDN = NH + 8;  // padded row strides (BF16 elements)
+constexpr int kTileSmem = (NF * LDN + NH * LDN + kTileRows * LDF + 4 * kTileRows * LDN) * 2 +
+                          (3 * NH + 2 * kTileRows + 8 + 2 * kTileThreads / 32) * 4;
+
+template <bool BWD>
+__global__ void __launch_bounds__(kTileThreads, 1)
+mlp_tile(const float* __restrict__ feat, const float* __restrict__ y, int B, const float* __restrict__ norm,
+         const float* __restrict__ P, const bf16* __restrict__ Wb, float* __restrict__ out,
+         float* __restrict__ part, float* __restrict__ loss_part) {
+    extern __shared__ __align__(128) unsigned char sm[];
+    bf16* W1s = (bf16*)sm;                 // [NF][LDN]
+    bf16* W2s = W1s + NF * LDN;            // [NH][LDN]
+    bf16* Xs = W2s + NH * LDN;             // [rows][LDF]
+    bf16* H1s = Xs + kTileRows * LDF;      // [rows][LDN]
+    bf16* H2s = H1s + kTileRows * LDN;
+    bf16* dZ2s = H2s + kTileRows * LDN;
+    bf16* dZ1s = dZ2s + kTileRows * LDN;
+    float* b1s = (float*)(dZ1s + kTileRows * LDN);
+    float* b2s = b1s + NH;
+    float* w3s = b2s + NH;
+    float* outs = w3s + NH;                // [rows]
+    float* douts = outs + kTileRows;       // [rows]
+    float* red = douts + kTileRows;        // [8] + per-warp sums
+    const int tid = threadIdx.x, lane = tid & 31, w = tid >> 5;
+    const int r0 = blockIdx.x * kTileRows;
+    const int rows = min(kTileRows, B - r0);
+
+    // stage the BF16 weights, the FP32 biases and the normalised inputs
+    for (int i = tid; i < NF * (NH / 8); i += kTileThreads) {
+        const int k = i / (NH / 8), c = i - k * (NH / 8);
+        *(int4*)(W1s + k * LDN + 8 * c) = *(const int4*)(Wb + k * NH + 8 * c);
     }
-}
-
-// out[b] = H2[b] . w3 + b3 (one warp per row, FP32)
-__global__ void head_fwd(const bf16* __restrict__ H2, int B, const float* __restrict__ P, float* __restrict__ out) {
-    const int row = (blockIdx.x * blockDim.x + threadIdx.x) >> 5, lane = threadIdx.x & 31;
-    if (row >= B) return;
-    float s = 0.f;
-    for (int n = lane; n < NH; n += 32) s += __bfloat162float(H2[row * NH + n]) * P[OFF_W3 + n];
-#pragma unroll
-    for (int o = 16; o > 0; o >>= 1) s += __shfl_xor_sync(0xffffffffu, s, o);
-    if (lane == 0) out[row] = s + P[OFF_B3];
-}
-
-// dout = 2 (out - y) / B; dZ2 = dout w3 (ReLU mask of H2)
-__global__ void head_bwd(const float* __restrict__ out, const float* __restrict__ y, int B,
-                         const bf16* __restrict__ H2, const float* __restrict__ P, float* __restrict__ dout,
-                         bf16* __restrict__ dZ2) {
-    const int i = blockIdx.x * blockDim.x + threadIdx.x;
-    if (i < B * NH) {
-        const int b = i / NH, n = i - b * NH;
-        const float d = 2.f * (out[b] - y[b]) / (float)B;
-        if (n == 0) dout[b] = d;
-        const float keep = __bfloat162float(H2[i]) > 0.f ? 1.f : 0.f;
-        dZ2[i] = __float2bfloat16(d * P[OFF_W3 + n] * keep);
+    for (int i = tid; i < NH * (NH / 8); i += kTileThreads) {
+        const int k = i / (NH / 8), c = i - k * (NH / 8);
+        *(int4*)(W2s + k * LDN + 8 * c) = *(const int4*)(Wb + NF * NH + k * NH + 8 * c);
     }
-}
-
-// column sums in fixed order: db[n] = sum_b D[b][n]; gw3[n] = sum_b H2[b][n] dout[b]; gb3 = sum dout
-__global__ void col_sums(const bf16* __restrict__ dZ1, const bf16* __restrict__ dZ2, const bf16* __restrict__ H2,
-                         const float* __restrict__ dout, int B, float* __restrict__ G) {
-    const int n = blockIdx.x * blockDim.x + threadIdx.x;
-    if (n < NH) {
-        float s1 = 0.f, s2 = 0.f, s3 = 0.f;
-        for (int b = 0; b < B; ++b) {
-            s1 += __bfloat162float(dZ1[b * NH + n]);
-            s2 += __bfloat162float(dZ2[b * NH + n]);
-            s3 += __bfloat162float(H2[b * NH + n]) * dout[b];
+    for (int i = tid; i < NH; i += kTileThreads) {
+        b1s[i] = P[OFF_B1 + i];
+        b2s[i] = P[OFF_B2 + i];
+        w3s[i] = P[OFF_W3 + i];
+    }
+    for (int i = tid; i < kTileRows * (NF / 4); i += kTileThreads) {
+        const int m = i / (NF / 4), c = i - m * (NF / 4);
+        float4 v = make_float4(0.f, 0.f, 0.f, 0.f);
+        if (m < rows) {
+            v = *(const float4*)(feat + (size_t)(r0 + m) * NF + 4 * c);
+            v.x = (v.x - norm[4 * c]) * norm[NF + 4 * c];
+            v.y = (v.y - norm[4 * c + 1]) * norm[NF + 4 * c + 1];
+            v.z = (v.z - norm[4 * c + 2]) * norm[NF + 4 * c + 2];
+            v.w = (v.w - norm[4 * c + 3]) * norm[NF + 4 * c + 3];
         }
-        G[OFF_B1 + n] = s1;
-        G[OFF_B2 + n] = s2;
-        G[OFF_W3 + n] = s3;
-    } else if (n == NH) {
-        float s = 0.f;
-        for (int b = 0; b < B; ++b) s += dout[b];
-        G[OFF_B3] = s;
+        __nv_bfloat162* d = (__nv_bfloat162*)(Xs + m * LDF + 4 * c);
+        d[0] = __floats2bfloat162_rn(v.x, v.y);
+        d[1] = __floats2bfloat162_rn(v.z, v.w);
     }
-}
-
-__global__ void mse(const float* __restrict__ out, const float* __restrict__ y, int B, float* loss) {
-    __shared__ float part[256];
-    float s = 0.f;
-    for (int b = threadIdx.x; b < B; b += blockDim.x) {
-        const float d = out[b] - y[b];
-        s += d * d;
-    }
-    part[threadIdx.x] = s;
     __syncthreads();
-    for (int w = blockDim.x / 2; w > 0; w >>= 1) {
-        if ((int)threadIdx.x < w) part[threadIdx.x] += part[threadIdx.x + w];
-        __syncthreads();
+
+    const int g = lane >> 2, t = lane & 3;
+    const int wm = (w & 3) * 16, wn = (w >> 2) * 64;  // 64 x 128 outputs: 4 x 2 warp tiles
+    // H = ReLU(A W + b), BF16, for the 64 x 128 warp-tiled outputs
+    auto dense_relu = [&](const bf16* A, int lda, const bf16* W, int K, const float* bias, bf16* H) {
+        float c[8][4] = {};
+        warp_mma<8, true, true>(c, A, lda, wm, W, LDN, wn, K, lane);
+#pragma unroll
+        for (int j = 0; j < 8; ++j) {
+            const int n = wn + 8 * j + 2 * t;
+#pragma unroll
+            for (int h = 0; h < 2; ++h) {
+                const float v0 = c[j][2 * h] + bias[n], v1 = c[j][2 * h + 1] + bias[n + 1];
+                *(__nv_bfloat162*)(H + (wm + g + 8 * h) * LDN + n) =
+                    __floats2bfloat162_rn(v0 > 0.f ? v0 : 0.f, v1 > 0.f ? v1 : 0.f);
+            }
+        }
+    };
+    dense_relu(Xs, LDF, W1s, NF, b1s, H1s);
+    __syncthreads();
+    dense_relu(H1s, LDN, W2s, NH, b2s, H2s);
+    __syncthreads();
+    // out = H2 w3 + b3 (FP32), 8 rows per warp
+    const float b3 = P[OFF_B3];
+    float se = 0.f;
+    for (int m = w * (kTileRows / 8); m < (w + 1) * (kTileRows / 8); ++m) {
+        float s = 0.f;
+        for (int n = lane; n < NH; n += 32) s = fmaf(__bfloat162float(H2s[m * LDN + n]), w3s[n], s);
+#pragma unroll
+        for (int o = 16; o > 0; o >>= 1) s += __shfl_xor_sync(0xffffffffu, s, o);
+        const float o_m = s + b3;
+        if (lane == 0) {
+            if (!BWD) {
+                if (m < rows) out[r0 + m] = o_m;
+            } else {
+                const float e = m < rows ? o_m - y[r0 + m] : 0.f;
+                outs[m] = o_m;
+                douts[m] = 2.f * e / (float)B;
+                se = fmaf(e, e, se);
+            }
+        }
     }
-    if (threadIdx.x == 0) *loss = part[0] / (float)B;
+    if (!BWD) return;
+    if (lane == 0) red[w] = se;
+    __syncthreads();
+    if (tid == 0) {
+        float l = 0.f;
+        for (int i = 0; i < kTileThreads / 32; ++i) l += red[i];
+        loss_part[blockIdx.x] = l;
+    }
+    // dZ2 = dout w3 [H2 > 0]  (BF16)
+    for (int i = tid; i < kTileRows * NH; i += kTileThreads) {
+        const int m = i / NH, n = i - m * NH;
+        const float keep = __bfloat162float(H2s[m * LDN + n]) > 0.f ? 1.f : 0.f;
+        dZ2s[m * LDN + n] = __float2bfloat16(douts[m] * w3s[n] * keep);
+    }
+    __syncthreads();
+    // dZ1 = (dZ2 W2^T) [H1 > 0]  (W2 stored [k][n] is W2^T stored [n][k])
+    {
+        float c[8][4] = {};
+        warp_mma<8, true, false>(c, dZ2s, LDN, wm, W2s, LDN, wn, NH, lane);
+#pragma unroll
+        for (int j = 0; j < 8; ++j) {
+            const int n = wn + 8 * j + 2 * t;
+#pragma unroll
+            for (int h = 0; h < 2; ++h) {
+                const int m = wm + g + 8 * h;
+                const float k0 = __bfloat162float(H1s[m * LDN + n]) > 0.f ? 1.f : 0.f;
+                const float k1 = __bfloat162float(H1s[m * LDN + n + 1]) > 0.f ? 1.f : 0.f;
+                *(__nv_bfloat162*)(dZ1s + m * LDN + n) = __floats2bfloat162_rn(c[j][2 * h] * k0, c[j][2 * h + 1] * k1);
+            }
+        }
+    }
+    __syncthreads();
+    float* G = part + (size_t)blockIdx.x * kPartStride;
+    // dW1 = X^T dZ1 (64 x 128, K = tile rows): 4 x 2 warp tiles
+    {
+        float c[8][4] = {};
+        warp_mma<8, false, true>(c, Xs, LDF, wm, dZ1s, LDN, wn, kTileRows, lane);
+#pragma unroll
+        for (int j = 0; j < 8; ++j) {
+            const int n = wn + 8 * j + 2 * t;
+#pragma unroll
+            for (int h = 0; h < 2; ++h)
+                *(float2*)(G + OFF_W1 + (wm + g + 8 * h) * NH + n) = make_float2(c[j][2 * h], c[j][2 * h + 1]);
+        }
+    }
+    // dW2 = H1^T dZ2 (128 x 128, K = tile rows): warp w takes rows 16 w
+    {
+        float c[16][4] = {};
+        warp_mma<16, false, true>(c, H1s, LDN, 16 * w, dZ2s, LDN, 0, kTileRows, lane);
+#pragma unroll
+        for (int j = 0; j < 16; ++j) {
+            const int n = 8 * j + 2 * t;
+#pragma unroll
+            for (int h = 0; h < 2; ++h)
+                *(float2*)(G + OFF_W2 + (16 * w + g + 8 * h) * NH + n) = make_float2(c[j][2 * h], c[j][2 * h + 1]);
+        }
+    }
+    // column sums: b1 = sum dZ1, b2 = sum dZ2, w3 = sum H2 dout, b3 = sum dout
+    if (tid < NH) {
+        float s1 = 0.f, s3 = 0.f;
+        for (int m = 0; m < rows; ++m) {
+            s1 += __bfloat162float(dZ1s[m * LDN + tid]);
+            s3 = fmaf(__bfloat162float(H2s[m * LDN + tid]), douts[m], s3);
+        }
+        G[OFF_B1 + tid] = s1;
+        G[OFF_W3 + tid] = s3;
+    } else {
+        const int n = tid - NH;
+        float s2 = 0.f, s4 = 0.f;
+        for (int m = 0; m < rows; ++m) {
+            s2 += __bfloat162float(dZ2s[m * LDN + n]);
+            s4 += douts[m];
+        }
+        G[OFF_B2 + n] = s2;
+        if (n == 0) G[OFF_B3] = s4;
+    }
+}
+
+// Gradients = the tiles' partials added in tile order; loss = their squared errors / B.
+__global__ void reduce_partials(const float* __restrict__ part, int T, float* __restrict__ G,
+                                const float* __restrict__ loss_part, float* __restrict__ loss, float inv_B) {
+    const int p = blockIdx.x * blockDim.x + threadIdx.x;
+    if (p < kMlpParams) {
+        float s = 0.f;
+        for (int i = 0; i < T; ++i) s += part[(size_t)i * kPartStride + p];
+        G[p] = s;
+    }
+    if (loss && p == 0) {
+        float l = 0.f;
+        for (int i = 0; i < T; ++i) l += loss_part[i];
+        *loss = l * inv_B;
+    }
 }
 
 __global__ void adam(float* __restrict__ P, const float* __restrict__ G, float* __restrict__ m, float* __restrict__ v,
@@ -197,45 +337,25 @@ static kn_status cuda_fail(cudaError_t e) { return noalloc_fail(KN_ERR_CUDA, cud
     } while (0)
 
 static kn_status ensure_cap(kn_mlp* m, int B) {
-    if (B <= m->cap) return KN_OK;
-    cudaFree(m->X);
-    cudaFree(m->H1);
-    cudaFree(m->H2);
-    cudaFree(m->dZ2);
-    cudaFree(m->dZ1);
-    cudaFree(m->out);
-    cudaFree(m->dout);
-    m->X = m->H1 = m->H2 = m->dZ2 = m->dZ1 = nullptr;
-    m->out = m->dout = nullptr;
-    m->cap = 0;
-    MC(cudaMalloc(&m->X, sizeof(bf16) * (size_t)B * NF));
-    MC(cudaMalloc(&m->H1, sizeof(bf16) * (size_t)B * NH));
-    MC(cudaMalloc(&m->H2, sizeof(bf16) * (size_t)B * NH));
-    MC(cudaMalloc(&m->dZ2, sizeof(bf16) * (size_t)B * NH));
-    MC(cudaMalloc(&m->dZ1, sizeof(bf16) * (size_t)B * NH));
-    MC(cudaMalloc(&m->out, sizeof(float) * (size_t)B));
-    MC(cudaMalloc(&m->dout, sizeof(float) * (size_t)B));
-    m->cap = B;
+    const int T = (B + kTileRows - 1) / kTileRows;
+    if (T <= m->cap_tiles) return KN_OK;
+    cudaFree(m->part);
+    cudaFree(m->loss_part);
+    m->part = m->loss_part = nullptr;
+    m->cap_tiles = 0;
+    MC(cudaMalloc(&m->part, sizeof(float) * (size_t)T * kPartStride));
+    MC(cudaMalloc(&m->loss_part, sizeof(float) * (size_t)T));
+    m->cap_tiles = T;
     return KN_OK;
 }
 
-static int gemm_grid(int M, int N) {
-    const long warps = (long)((M + 15) / 16) * ((N + 7) / 8);
-    return (int)((warps * 32 + 127) / 128);
-}
-
-static kn_status forward(kn_mlp* m, const float* feat, int B, cudaStream_t st) {
-    kn_status s = ensure_cap(m, B);
-    if (s != KN_OK) return s;
-    prep_x<<<(B * NF + 255) / 256, 256, 0, st>>>(feat, B, m->norm, m->X);
-    const bf16* W1 = m->Wb;
-    const bf16* W2 = m->Wb + NF * NH;
-    gemm_bf16<EPI_RELU_BF16><<<gemm_grid(B, NH), 128, 0, st>>>(B, NH, NF, m->X, NF, 1, W1, NH, 1, m->P + OFF_B1,
-                                                               m->H1, NH, nullptr, 0);
-    gemm_bf16<EPI_RELU_BF16><<<gemm_grid(B, NH), 128, 0, st>>>(B, NH, NH, m->H1, NH, 1, W2, NH, 1, m->P + OFF_B2,
-                                                               m->H2, NH, nullptr, 0);
-    head_fwd<<<(B * 32 + 127) / 128, 128, 0, st>>>(m->H2, B, m->P, m->out);
-    MC(cudaGetLastError());
+static kn_status tile_smem_limit() {
+    static bool done = false;
+    if (!done) {
+        MC(cudaFuncSetAttribute(mlp_tile<false>, cudaFuncAttributeMaxDynamicSharedMemorySize, kTileSmem));
+        MC(cudaFuncSetAttribute(mlp_tile<true>, cudaFuncAttributeMaxDynamicSharedMemorySize, kTileSmem));
+        done = true;
+    }
     return KN_OK;
 }
 
@@ -275,8 +395,7 @@ kn_status kn_mlp_destroy(kn_mlp* m) {
     if (!m) return KN_OK;
     cudaDeviceSynchronize();
     for (void* p : {(void*)m->P, (void*)m->G, (void*)m->Am, (void*)m->Av, (void*)m->Wb, (void*)m->norm,
-                    (void*)m->X, (void*)m->H1, (void*)m->H2, (void*)m->dZ2, (void*)m->dZ1, (void*)m->out,
-                    (void*)m->dout})
+                    (void*)m->part, (void*)m->loss_part})
         if (p) cudaFree(p);
     delete m;
     return KN_OK;
@@ -314,31 +433,27 @@ kn_status kn_mlp_get_params(const kn_mlp* m, float* params, float* grads) {
 
 kn_status kn_mlp_forward(kn_mlp* m, const float* feat, int32_t B, float* out, void* stream) {
     if (!m || !feat || !out || B < 1) return noalloc_fail(KN_ERR_INVALID_ARG, "kn_mlp_forward: bad arguments");
-    cudaStream_t st = (cudaStream_t)stream;
-    kn_status s = forward(m, feat, B, st);
+    if ((uintptr_t)feat & 15) return noalloc_fail(KN_ERR_INVALID_ARG, "kn_mlp_forward: features must be 16-byte aligned");
+    kn_status s = tile_smem_limit();
     if (s != KN_OK) return s;
-    MC(cudaMemcpyAsync(out, m->out, sizeof(float) * B, cudaMemcpyDeviceToDevice, st));
+    const int T = (B + kTileRows - 1) / kTileRows;
+    mlp_tile<false><<<T, kTileThreads, kTileSmem, (cudaStream_t)stream>>>(feat, nullptr, B, m->norm, m->P, m->Wb,
+                                                                         out, nullptr, nullptr);
+    MC(cudaGetLastError());
     return KN_OK;
 }
 
 kn_status kn_mlp_backward(kn_mlp* m, const float* feat, const float* y, int32_t B, float* loss, void* stream) {
     if (!m || !feat || !y || B < 1) return noalloc_fail(KN_ERR_INVALID_ARG, "kn_mlp_backward: bad arguments");
+    if ((uintptr_t)feat & 15) return noalloc_fail(KN_ERR_INVALID_ARG, "kn_mlp_backward: features must be 16-byte aligned");
     cudaStream_t st = (cudaStream_t)stream;
-    kn_status s = forward(m, feat, B, st);
+    kn_status s = tile_smem_limit();
     if (s != KN_OK) return s;
-    if (loss) mse<<<1, 256, 0, st>>>(m->out, y, B, loss);
-    head_bwd<<<(B * NH + 255) / 256, 256, 0, st>>>(m->out, y, B, m->H2, m->P, m->dout, m->dZ2);
-    const bf16* W2 = m->Wb + NF * NH;
-    // dW2 = H1^T dZ2
-    gemm_bf16<EPI_F32><<<gemm_grid(NH, NH), 128, 0, st>>>(NH, NH, B, m->H1, 1, NH, m->dZ2, NH, 1, nullptr,
-                                                          m->G + OFF_W2, NH, nullptr, 0);
-    // dZ1 = (dZ2 W2^T) * [H1 > 0]
-    gemm_bf16<EPI_MASK_BF16><<<gemm_grid(B, NH), 128, 0, st>>>(B, NH, NH, m->dZ2, NH, 1, W2, 1, NH, nullptr, m->dZ1,
-                                                               NH, m->H1, NH);
-    // dW1 = X^T dZ1
-    gemm_bf16<EPI_F32><<<gemm_grid(NF, NH), 128, 0, st>>>(NF, NH, B, m->X, 1, NF, m->dZ1, NH, 1, nullptr,
-                                                          m->G + OFF_W1, NH, nullptr, 0);
-    col_sums<<<1, 160, 0, st>>>(m->dZ1, m->dZ2, m->H2, m->dout, B, m->G);
+    if ((s = ensure_cap(m, B)) != KN_OK) return s;
+    const int T = (B + kTileRows - 1) / kTileRows;
+    mlp_tile<true><<<T, kTileThreads, kTileSmem, st>>>(feat, y, B, m->norm, m->P, m->Wb, nullptr, m->part,
+                                                       m->loss_part);
+    reduce_partials<<<(kMlpParams + 255) / 256, 256, 0, st>>>(m->part, T, m->G, m->loss_part, loss, 1.f / (float)B);
     MC(cudaGetLastError());
     return KN_OK;
 }

@@ -62,9 +62,12 @@ def init_params(seed: int = 0) -> np.ndarray:
 
 
 def train_network(feat, lab, epochs: int = 4, batch: int = 4096, lr: float = 1e-3, seed: int = 0,
-                  stream=None):
+                  stream=None, time_kernels: bool = False):
     """Train a fresh network on the records with the library's GPU kernels
-    (mean squared error, Adam).  Returns (network, per-epoch mean loss)."""
+    (mean squared error, Adam).  Each epoch shuffles the records once on the
+    GPU; batches are then contiguous slices.  Returns (network, per-epoch
+    mean loss), plus with time_kernels the seconds the training kernels
+    themselves took (CUDA events around each batch's backward and Adam)."""
     import torch
     mu, sd = normalisation(feat)
     net = kn.MLP()
@@ -72,18 +75,27 @@ def train_network(feat, lab, epochs: int = 4, batch: int = 4096, lr: float = 1e-
     n = feat.shape[0]
     gen = torch.Generator(device=feat.device)
     gen.manual_seed(seed)
-    loss = torch.zeros(1, dtype=torch.float32, device=feat.device)
+    losses = torch.zeros(max(1, n // batch), dtype=torch.float32, device=feat.device)
     history = []
+    events = []
+    st = stream if stream is not None else torch.cuda.current_stream()
     for _ in range(epochs):
         perm = torch.randperm(n, device=feat.device, generator=gen)
-        tot, cnt = 0.0, 0
+        xs = feat.index_select(0, perm)
+        ys = lab.index_select(0, perm)
+        nb = 0
         for i in range(0, n - batch + 1, batch):
-            idx = perm[i:i + batch]
-            xb = feat.index_select(0, idx).contiguous()
-            yb = lab.index_select(0, idx).contiguous()
-            net.backward(xb, yb, loss, stream)
+            if time_kernels:
+                e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+                e0.record(st)
+            net.backward(xs[i:i + batch], ys[i:i + batch], losses[nb:nb + 1], stream)
             net.adam(lr, stream=stream)
-            tot += float(loss.item()) if (cnt % 64 == 0) else 0.0
-            cnt += 1
-        history.append(tot / max(1, (cnt + 63) // 64))
+            if time_kernels:
+                e1.record(st)
+                events.append((e0, e1))
+            nb += 1
+        history.append(float(losses[:nb].mean().item()))
+    if time_kernels:
+        torch.cuda.synchronize()
+        return net, history, sum(a.elapsed_time(b) for a, b in events) / 1e3
     return net, history

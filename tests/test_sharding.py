@@ -58,3 +58,55 @@ def test_zone_slice_bounds():
     assert shard.zone_slice(3, 4, 10) == (30, 40)
     with pytest.raises(ValueError):
         shard.zone_slice(4, 4, 10)
+
+
+def _strong_worker(rank, world, port, out):
+    import torch.distributed as dist
+    os.environ["MASTER_ADDR"] = "127.0.0.1"
+    os.environ["MASTER_PORT"] = str(port)
+    dist.init_process_group("gloo", rank=rank, world_size=world)
+    from kn_inputs import net150, profile_zones
+    from paper_1409_5826_gb300 import shard
+    whole = profile_zones(net150(), 37)
+    parts = shard.balanced_partition(shard.cost_key(net150(), whole), world)
+    out[rank] = parts[rank].tolist()
+    dist.barrier()
+    dist.destroy_process_group()
+
+
+def test_strong_partition_two_ranks_cover_the_batch():
+    """Each rank computes the cost-balanced split on its own; together the
+    ranks hold every zone of the batch exactly once, sizes within one."""
+    import torch.multiprocessing as mp
+    ctx = mp.get_context("spawn")
+    out = ctx.Manager().dict()
+    port = _free_port()
+    procs = [ctx.Process(target=_strong_worker, args=(r, 2, port, out)) for r in range(2)]
+    for p in procs:
+        p.start()
+    for p in procs:
+        p.join(timeout=120)
+        assert p.exitcode == 0
+    allz = sorted(out[0] + out[1])
+    assert allz == list(range(37))
+    assert abs(len(out[0]) - len(out[1])) <= 1
+
+
+def test_strong_partition_balances_oracle_steps(oracle_mod):
+    """The serpentine deal by predicted cost balances the measured work (the
+    oracle's accepted steps) far better than contiguous slices of the batch
+    sorted by that cost would, and about as well as a random split."""
+    from kn_inputs import net150, profile_zones
+    from paper_1409_5826_gb300 import shard
+    net = net150()
+    z = profile_zones(net, 48, t_end=2e-11)
+    steps = oracle_mod.Oracle(net).integrate_batch(z, threads=8)["steps"].astype(float)
+    key = shard.cost_key(net, z)
+    assert np.corrcoef(key, steps)[0, 1] > 0.5  # the key predicts the cost
+    for world in (2, 4):
+        parts = shard.balanced_partition(key, world)
+        loads = np.array([steps[p].sum() for p in parts])
+        order = np.argsort(-key)
+        contiguous = np.array([steps[c].sum() for c in np.array_split(order, world)])
+        assert loads.max() / loads.mean() < 1.15, loads
+        assert loads.max() / loads.mean() < contiguous.max() / contiguous.mean()
