@@ -757,6 +757,12 @@ def main():
         roof = fp64_roofline(algorithmic_flops(net, st["steps"], st["rejects"]), kms, kn.measure_fp64_peak(stream),
                              "rates 5 R + fluxes 1/3/7 per 1/2/3-body reaction + gathers S_r + S_p per accepted "
                              "step, 11 N per attempt")
+    elif args.form == "mixed_fp64":
+        # bound by the FP64 pipe (the update, the conservation sum and the
+        # widening of F+ and k); the shared-memory figure rides along
+        roof = fp64_roofline(update_fp64_flops(net, st["steps"] + st["rejects"]), kms, kn.measure_fp64_peak(stream),
+                             "11 FP64 operations per species per attempt (update, conservation sum, test)")
+        roof["smem"] = smem_roofline([(net, st["steps"], st["rejects"])], kms, clk, n_sms)
     else:
         # SM-local bound: shared-memory bandwidth, 32 banks x 4 B per clock per
         # SM at the SM clock sampled during the timed steps

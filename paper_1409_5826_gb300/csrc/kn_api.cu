@@ -396,6 +396,7 @@ static void set_guard_band(OptsDev& D, const kn_opts* o) {
     D.ga32 = (float)(o->safety * o->eps_r);
     D.gb32 = (float)(o->safety * o->eps_c);
     D.grow32 = (float)o->grow_max;
+    D.shrink32 = (float)o->shrink;
     D.band_lo32 = (float)(1.0 - band);
     D.band_hi32 = (float)(1.0 + band);
     D.thr_lo32 = (float)(o->eps_r * (1.0 - band));

@@ -161,30 +161,23 @@ struct GroupPtrs {
 
 // (d) kappa-switched update (Sec. 3, Eq. 3) with step h from buffer cur into
 // nxt, and each warp's share of the error measures (no barrier inside).
-// FP64 form (R = double): every step in FP64, in the order of the
-// definitions.  Mixed form with the FP64 update (R = float): F+ and k arrive
-// in FP32 and are widened; the update, the conservation sum and the test run
-// in FP64 exactly as in the FP64 form, and an FP32 copy of y' is kept for the
-// FP32 flux pass.
-template <class R>
+// FP64 form: every step in FP64, in the order of the definitions.
 __device__ __forceinline__ void update_reduce_fp64(const PlanDev& P, const OptsDev& O, const GroupPtrs& g, int lane,
                                                    int cur, double h, int z) {
     const int N = P.N, G = P.G, NP1 = N + 1;
-    const R* Fk = (const R*)g.Fk;
-    const R* A = (const R*)g.A;
+    const double* Fk = (const double*)g.Fk;
+    const double* A = (const double*)g.A;
     const double* Yc = g.Y64 + cur * NP1;
     double* Yn64 = g.Y64 + (cur ^ 1) * NP1;
-    [[maybe_unused]] float* Yn32 = g.Y32 + (cur ^ 1) * NP1;
     const double kappa = O.kappa, ymin = O.y_min;
     double csum = 0.0, bn = 0.0, bd = 1.0;
     for (int i = lane; i < N; i += G) {
-        const double y = Yc[i], fp = (double)Fk[2 * i], kk = (double)Fk[2 * i + 1];
+        const double y = Yc[i], fp = Fk[2 * i], kk = Fk[2 * i + 1];
         const double kdt = kk * h;
         const double yn = (kdt >= kappa) ? (y + h * fp) / (1.0 + kdt) : y + h * (fp - kk * y);
         Yn64[i] = yn;
-        if (sizeof(R) == 4) Yn32[i] = (float)yn;
         const double d = yn - y;
-        csum = fma((double)A[i], d, csum);
+        csum = fma(A[i], d, csum);
         if ((y > yn ? y : yn) > ymin) {
             const double m = y > yn ? y : yn;
             const double ad = fabs(d);
@@ -235,7 +228,7 @@ __device__ __forceinline__ void two_sum(float a, float b, float& s, float& e) {
 // sum A (y' - y) is a float-float sum of exact products, so it resolves the
 // stored change far below eps_c; no FP64 instruction runs per species.
 __device__ __forceinline__ void update_reduce_mixed(const PlanDev& P, const OptsDev& O, const GroupPtrs& g, int lane,
-                                                    int cur, double h, int z) {
+                                                    int cur, float h32, int z) {
     const int N = P.N, G = P.G, NP1 = N + 1;
     const float2* Fk = (const float2*)g.Fk;  // (F+_i, k_i)
     const float* A = (const float*)g.A;
@@ -243,7 +236,6 @@ __device__ __forceinline__ void update_reduce_mixed(const PlanDev& P, const Opts
     const float* Yl = g.Ylo + cur * NP1;
     float* Nh = g.Y32 + (cur ^ 1) * NP1;
     float* Nl = g.Ylo + (cur ^ 1) * NP1;
-    const float h32 = (float)h;
     float cs_h = 0.f, cs_l = 0.f, rmax = 0.f;
     int ok = 1;
     // species i; FIRST: the lane's first species starts the sums
@@ -333,15 +325,84 @@ __device__ __forceinline__ void update_reduce_mixed(const PlanDev& P, const Opts
     }
 }
 
+// Mixed form with the FP64 update: F+ and k arrive from the Kahan-compensated
+// FP32 gathers and are widened; the kappa-switched update runs in FP64 on FP64
+// abundances (an FP32 copy of y' is kept for the FP32 flux pass), and the
+// conservation sum sum A (y' - y) is an FP64 sum.  The relative test's
+// decisions are those of the FP64 compares max(y, y') > y_min and
+// |y' - y| <= eps_r max(y, y'): taken on the FP32 copies when these lie
+// outside a guard band that bounds the copies' rounding and the ratio's
+// division (as in the mixed form), and in FP64 inside it.  Per warp the
+// reductions carry the FP64 sum, an all-pass flag and the FP32 maximum ratio
+// (the step proposal), so no FP64 compare or product runs in them.
+__device__ __forceinline__ void update_reduce_mixed64(const PlanDev& P, const OptsDev& O, const GroupPtrs& g,
+                                                      int lane, int cur, double h, int z) {
+    const int N = P.N, G = P.G, NP1 = N + 1;
+    const float2* Fk = (const float2*)g.Fk;  // (F+_i, k_i)
+    const double* A = (const double*)g.A;
+    const double* Yc = g.Y64 + cur * NP1;
+    const float* Yc32 = g.Y32 + cur * NP1;
+    double* Yn64 = g.Y64 + (cur ^ 1) * NP1;
+    float* Yn32 = g.Y32 + (cur ^ 1) * NP1;
+    const double kappa = O.kappa;
+    double csum = 0.0;
+    float rmax = 0.f;
+    int ok = 1;
+    for (int i = lane; i < N; i += G) {
+        const float2 fk = Fk[i];
+        const double y = Yc[i], fp = (double)fk.x, kk = (double)fk.y;
+        const double kdt = kk * h;
+        const double yn = (kdt >= kappa) ? (y + h * fp) / (1.0 + kdt) : y + h * (fp - kk * y);
+        const float yn32 = (float)yn;
+        Yn64[i] = yn;
+        Yn32[i] = yn32;
+        const double d = yn - y;
+        csum = fma(A[i], d, csum);
+        // y32 = fl32(y) and yn32 = fl32(y'): each within 2^-24 relative, so the
+        // band of set_guard_band covers their difference and the ratio
+        const float y32 = Yc32[i];
+        const float m32 = fmaxf(y32, yn32);
+        int tested;
+        if (m32 > O.ymin_hi32) tested = 1;
+        else if (m32 < O.ymin_lo32) tested = 0;
+        else tested = (y > yn ? y : yn) > O.y_min;
+        if (tested) {
+            const float r = __fdividef(fabsf(__fsub_rn(yn32, y32)), m32);
+            int pass_i;
+            if (r < O.thr_lo32) pass_i = 1;
+            else if (r > O.thr_hi32) pass_i = 0;
+            else pass_i = fabs(d) <= O.eps_r * (y > yn ? y : yn);
+            ok &= pass_i;
+            rmax = fmaxf(rmax, r);
+        }
+        if (O.probe) {
+            O.probe_Fp[(size_t)z * N + i] = fp;
+            O.probe_k[(size_t)z * N + i] = kk;
+            O.probe_Y1[(size_t)z * N + i] = yn;
+        }
+    }
+#pragma unroll
+    for (int off = 16; off > 0; off >>= 1) csum += __shfl_xor_sync(0xffffffffu, csum, off);
+    const unsigned int rbits = __reduce_max_sync(0xffffffffu, __float_as_uint(rmax));
+    ok = __all_sync(0xffffffffu, ok);
+    if ((lane & 31) == 0) {
+        const int w = lane >> 5;
+        g.red_c[w] = csum;
+        g.red_r[w] = __uint_as_float(rbits);
+        g.red_f[w] = ok;
+    }
+}
+
+// h: the step (FP64 forms); h32: the same step in FP32 (the mixed form's update)
 template <int PREC>
 __device__ __forceinline__ void update_reduce(const PlanDev& P, const OptsDev& O, const GroupPtrs& g, int lane,
-                                              int cur, double h, int z) {
+                                              int cur, double h, float h32, int z) {
     if (PREC == kPrecMixed)
-        update_reduce_mixed(P, O, g, lane, cur, h, z);
+        update_reduce_mixed(P, O, g, lane, cur, h32, z);
     else if (PREC == kPrecMixed64)
-        update_reduce_fp64<float>(P, O, g, lane, cur, h, z);
+        update_reduce_mixed64(P, O, g, lane, cur, h, z);
     else
-        update_reduce_fp64<double>(P, O, g, lane, cur, h, z);
+        update_reduce_fp64(P, O, g, lane, cur, h, z);
 }
 
 // lane 0, after the barrier that follows update_reduce: combine the warps.
@@ -372,6 +433,18 @@ __device__ __forceinline__ TestOutcome combine(const PlanDev& P, const OptsDev& 
         v.fin = isfinite(cs) ? 1 : 0;
         v.cons32 = fabsf(cs);
         v.pass = v.fin && ok && v.cons32 <= O.eps_c32;
+    } else if (PREC == kPrecMixed64) {
+        double cs = 0.0;
+        int ok = 1;
+        for (int w = 0; w < nw; ++w) {
+            cs += g.red_c[w];
+            v.rmax = fmaxf(v.rmax, g.red_r[w]);
+            ok &= g.red_f[w];
+        }
+        v.fin = isfinite(cs) ? 1 : 0;
+        v.cons = fabs(cs);
+        v.cons32 = (float)v.cons;
+        v.pass = v.fin && ok && v.cons <= O.eps_c;
     } else {
         double cs = 0.0;
         for (int w = 0; w < nw; ++w) {
@@ -387,6 +460,85 @@ __device__ __forceinline__ TestOutcome combine(const PlanDev& P, const OptsDev& 
         v.pass = v.fin && v.cons <= O.eps_c && v.bn <= O.eps_r * v.bd;
     }
     return v;
+}
+
+// lane 0, mixed form, plain integration (no probe, no replay): accept or
+// reject the attempt just tested and set up the next one.  The step sizes are
+// FP32 (the mixed update takes h in FP32 anyway) and the time axis FP64.  The
+// FP64 work that does not depend on the outcome -- the time an accept would
+// reach, the remaining interval after an accept or a reject, the profile
+// factor there -- is issued before the warp combine so that its latency
+// overlaps it; after the combine the chain to the next step is FP32 only.
+// Clipping to t_end compares in FP32; a step that an FP32 compare leaves a
+// hair past t_end ends the zone at t_end all the same.
+template <bool FEAT>
+__device__ __forceinline__ void decide_mixed(GroupState& S, const PlanDev& P, const OptsDev& O, const GroupPtrs& g,
+                                             int nxt, bool spec) {
+    const float h32 = S.h32;
+    const double t = S.t, te = S.t_end;
+    const int was_clipped = S.clipped;
+    const double t_acc = was_clipped ? te : t + (double)h32;
+    const float rem_acc = (float)(te - t_acc);
+    const float rem_cur = (float)(te - t);
+    const float u_acc = S.constant ? 0.f : __fmul_rn(__double2float_rn(t_acc), S.u_scale);
+    if (spec && S.refresh_spec) S.u_ref = S.u_spec;  // the speculative pass refreshed Kc
+    const TestOutcome v = combine<kPrecMixed>(P, O, g);
+    if (v.pass) {
+        const float ga = __fdiv_rn(O.ga32, fmaxf(v.rmax, 1e-30f));
+        const float gb = __fdiv_rn(O.gb32, fmaxf(v.cons32, 1e-30f));
+        const float dt = __fmul_rn(h32, fminf(O.grow32, fminf(ga, gb)));
+        S.dt32 = dt;
+        S.dtp32 = dt;
+        S.cur = nxt;
+        S.steps += 1;
+        S.nrej = 0;
+        S.rhs_valid = 0;
+        if (FEAT) {
+            if (S.mlp_try) S.props += 1;
+            S.mlp_try = 0;
+            S.h_prev = (double)h32;
+            S.dt_plain = (double)dt;
+            S.fresh = 1;
+        }
+        if (was_clipped || !(t_acc < te)) {
+            S.t = te;
+            S.done = 1;
+        } else {
+            S.t = t_acc;
+            S.u = u_acc;
+            if (S.steps >= O.max_steps) {
+                S.status = 1;  // STEP_LIMIT
+                S.done = 1;
+            } else {
+                const int c = dt >= rem_acc;
+                S.clipped = c;
+                S.h32 = c ? rem_acc : dt;
+            }
+        }
+    } else {
+        S.rejects += 1;
+        S.rhs_valid = 1;
+        float dt;
+        if (FEAT && S.mlp_try) {
+            // a rejected learned proposal: retry with the plain controller's dt
+            S.mlp_try = 0;
+            dt = S.dtp32;
+        } else {
+            S.nrej += 1;
+            dt = __fmul_rn(h32, O.shrink32);
+            if (S.nrej > O.max_reject) {
+                S.status = v.fin ? 4 : 3;  // MAX_REJECT : NONFINITE
+                S.done = 1;
+            } else if ((double)dt < O.dt_min_frac * t) {
+                S.status = 2;  // DT_UNDERFLOW
+                S.done = 1;
+            }
+        }
+        S.dt32 = dt;
+        const int c = dt >= rem_cur;
+        S.clipped = c;
+        S.h32 = c ? rem_cur : dt;
+    }
 }
 
 // FP32 exponent histogram bin (4 octaves per bin, values below 2^-100 in bin 0)
@@ -750,7 +902,14 @@ __device__ void run_group(const PlanDev& P, const OptsDev& O, const unsigned cha
                 K[j] = (real)exp(fma(p.y, lnT0, p.x) + r1 * lnR0);
             }
         }
-        if (lane == 0) leader_prepare<PREC>(S, P, O);
+        if (lane == 0) {
+            leader_prepare<PREC>(S, P, O);
+            if (PREC == kPrecMixed) {
+                S.h32 = (float)S.h;
+                S.dt32 = (float)S.dt;
+                S.dtp32 = S.dt32;
+            }
+        }
         gs.sync();
 
         // ---- step loop (Sec. 4: adaptive network timesteps) ----
@@ -865,7 +1024,7 @@ __device__ void run_group(const PlanDev& P, const OptsDev& O, const unsigned cha
                         const double rem = S.t_end - S.t;
                         const bool last = hq >= rem;
                         if (last) hq = rem;
-                        update_reduce<PREC>(P, O, g, lane, cur, hq, z);
+                        update_reduce<PREC>(P, O, g, lane, cur, hq, (float)hq, z);
                         gs.sync();
                         if (lane == 0) {
                             const TestOutcome v = combine<PREC>(P, O, g);
@@ -889,6 +1048,7 @@ __device__ void run_group(const PlanDev& P, const OptsDev& O, const unsigned cha
                                 const double rem = S.t_end - S.t;
                                 S.clipped = hb >= rem;
                                 S.h = S.clipped ? rem : hb;
+                                if (PREC == kPrecMixed) S.h32 = (float)S.h;
                                 S.mlp_try = S.h > lo;
                             }
                         }
@@ -907,6 +1067,7 @@ __device__ void run_group(const PlanDev& P, const OptsDev& O, const unsigned cha
                             const double rem = S.t_end - S.t;
                             S.clipped = hm >= rem;
                             S.h = S.clipped ? rem : hm;
+                            if (PREC == kPrecMixed) S.h32 = (float)S.h;
                             S.mlp_try = S.h > lo;  // clipping to t_end can leave only the plain step
                         }
                         if (O.trace_out) {
@@ -919,7 +1080,7 @@ __device__ void run_group(const PlanDev& P, const OptsDev& O, const unsigned cha
                                 d[0] = S.h_prev;
                                 d[1] = S.dt_plain;
                                 d[2] = raw;
-                                d[3] = S.h;
+                                d[3] = PREC == kPrecMixed ? (double)S.h32 : S.h;  // the step the update takes
                                 d[4] = S.mlp_try ? 1.0 : 0.0;
                                 d[5] = S.t_end - S.t;
                             }
@@ -933,24 +1094,26 @@ __device__ void run_group(const PlanDev& P, const OptsDev& O, const unsigned cha
             // (d) update and error measures, then (e) the decision (lane 0)
             // while warps 1.. compute (a) for the candidate state at t + h,
             // as the next step needs it if this one is accepted
-            const double h_now = S.h;
+            const double h_now = PREC == kPrecMixed ? (double)S.h32 : S.h;
             if (spec && lane == 32) {
                 // the candidate state's profile factor (t + h) / (tau ln 2), once per group
                 S.u_spec = S.constant ? 0.f : __fmul_rn(__double2float_rn(S.t + h_now), S.u_scale);
                 S.refresh_spec = !P.rate_cache || !(fabsf(S.u_spec - S.u_ref) <= P.u_tol);
             }
-            update_reduce<PREC>(P, O, g, lane, cur, h_now, z);
+            update_reduce<PREC>(P, O, g, lane, cur, h_now, PREC == kPrecMixed ? S.h32 : (float)h_now, z);
             gs.sync();
             if (spec && lane >= 32)
                 flux_pass<PREC>(P, g, lane - 32, G - 32, nxt, S.constant, 0.0, S.u_spec, 0, S.refresh_spec != 0);
             have_a = spec;
-            if (lane == 0) {
+            if (PREC == kPrecMixed && lane == 0 && !O.probe && !O.replay_dt) {
+                decide_mixed<FEAT>(S, P, O, g, nxt, spec);
+            } else if (lane == 0) {
                 if (spec && S.refresh_spec) S.u_ref = S.u_spec;  // the speculative pass refreshed Kc
                 const TestOutcome v = combine<PREC>(P, O, g);
-                const double h = S.h;
+                const double h = S.h;  // FP64 (replay steps are FP64 even in the mixed form)
                 if (O.probe) {
                     O.probe_cons[z] = PREC == kPrecMixed ? (double)v.cons32 : v.cons;
-                    O.probe_rel[z] = PREC == kPrecMixed ? (double)v.rmax : v.bn / v.bd;
+                    O.probe_rel[z] = PREC == kPrecFP64 ? v.bn / v.bd : (double)v.rmax;
                     S.done = 1;
                 } else if (O.replay_dt || v.pass) {
                     S.t = S.clipped ? S.t_end : S.t + h;
@@ -964,7 +1127,7 @@ __device__ void run_group(const PlanDev& P, const OptsDev& O, const unsigned cha
                     S.fresh = 1;
                     if (O.replay_dt) {
                         S.dt = h;
-                    } else if (PREC != kPrecMixed) {
+                    } else if (PREC == kPrecFP64) {
                         // FP64 form: the proposal in FP64 as well
                         const double rel = v.bn / v.bd;
                         double gfac = O.grow_max;
@@ -974,7 +1137,7 @@ __device__ void run_group(const PlanDev& P, const OptsDev& O, const unsigned cha
                         if (gb < gfac) gfac = gb;
                         S.dt = h * gfac;
                     } else {
-                        // mixed form: the growth factor in FP32
+                        // FP32-flux forms: the growth factor in FP32
                         const float ga = __fdiv_rn(O.ga32, fmaxf(v.rmax, 1e-30f));
                         const float gb = __fdiv_rn(O.gb32, fmaxf(v.cons32, 1e-30f));
                         const float gfac = fminf(O.grow32, fminf(ga, gb));
@@ -1001,6 +1164,10 @@ __device__ void run_group(const PlanDev& P, const OptsDev& O, const unsigned cha
                     }
                 }
                 leader_prepare<PREC>(S, P, O);
+                if (PREC == kPrecMixed) {
+                    S.h32 = (float)S.h;
+                    S.dt32 = (float)S.dt;
+                }
             }
             gs.sync();
         }
@@ -1039,7 +1206,7 @@ __device__ void run_group(const PlanDev& P, const OptsDev& O, const unsigned cha
             }
             if (lane == 0) {
                 P.t_out[z] = S.t;
-                P.dt_next[z] = S.dt;
+                P.dt_next[z] = PREC == kPrecMixed ? (double)S.dt32 : S.dt;
                 P.steps[z] = S.steps;
                 P.rejects[z] = S.rejects;
                 if (P.props) P.props[z] = S.props;

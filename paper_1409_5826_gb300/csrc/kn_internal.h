@@ -45,7 +45,8 @@ constexpr int kMlpSmemBytes = (kMlpFeatures * kMlpHidden + kMlpHidden * kMlpHidd
 // that the flux loop is warp-uniform and multiplies by no sentinel.
 struct TableLayout {
     int32_t bytes;        // total (multiple of 16)
-    int32_t off_A;        // real[N] (mass numbers; integers, exact in FP32)
+    int32_t off_A;        // mass numbers (integers, exact): float[N] in the mixed form, double[N] in the
+                          //   forms with an FP64 update
     int32_t off_rspec;    // uint32[R]: reactant species a | b << 10 | c << 20 (N = none)
     int32_t off_cexp;     // real[R]: c_j = n_j + 3 (r_j - 1), so that along the profile
                           //   k_j(t) = k_j(T0, rho0) exp(-c_j t / tau)
@@ -100,6 +101,11 @@ struct GroupState {
     int refresh_spec;  // the speculative flux pass recomputes Kc
     double h_best;     // label search: the last grid step that passed (0: none)
     long long t_fetch_ns;  // global timer when the zone was taken from the queue
+    // mixed form: the step sizes in FP32 (the update runs in FP32 and takes h as FP32)
+    float h32;      // the current attempt's step
+    float dt32;     // the controller's next step
+    float dtp32;    // the plain controller's proposal for the current state
+    float pad3;
 };
 
 struct PlanDev {
@@ -170,6 +176,7 @@ struct OptsDev {
     // FP32 guard band of the mixed form's accept test (see update_reduce)
     float eps_r32, ymin_lo32, ymin_hi32, band_lo32, band_hi32, kappa32;
     float eps_c32, ga32, gb32, grow32;  // mixed form: eps_c and the growth factor's terms in FP32
+    float shrink32;                     // mixed form: the reject factor in FP32
     float thr_lo32, thr_hi32;           // mixed form: eps_r times the guard band's ends
     // trace of the learned proposal: features [cap][64], output [cap], dt record [cap][6]
     float* trace_feat;

@@ -298,10 +298,11 @@ kn_status build_tables_host(const kn_network* n, int prec, int Q, std::vector<un
         }
     }
     const int real = prec == kPrecFP64 ? 8 : 4;
+    const int a_bytes = prec == kPrecMixed ? 4 : 8;  // A is read by the update: FP64 where the update is
     TableLayout tl{};
     int off = 0;
     tl.off_A = off;
-    off = pad16(off + real * N);
+    off = pad16(off + a_bytes * N);
     tl.off_rspec = off;
     off = pad16(off + 4 * R);
     tl.off_cexp = off;
@@ -317,7 +318,7 @@ kn_status build_tables_host(const kn_network* n, int prec, int Q, std::vector<un
     tl.bytes = off;
     blob.assign(off, 0);
     for (int i = 0; i < N; ++i) {
-        if (prec == kPrecFP64) {
+        if (a_bytes == 8) {
             memcpy(blob.data() + tl.off_A + 8 * i, &n->A[i], 8);
         } else {
             const float af = (float)n->A[i];

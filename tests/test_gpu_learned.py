@@ -173,10 +173,14 @@ def test_in_integrator_inference_matches_oracle(env, margin):
     e = np.exp(np.minimum(out.astype(np.float32) - np.float32(margin), np.float32(20.0)).astype(np.float64))
     assert np.allclose(raw, h_prev * e, rtol=4e-7, atol=0)
     # then exactly: clip to [dt_plain, 16 dt_plain], then to t_end; a proposal
-    # not above dt_plain leaves the plain attempt min(dt_plain, t_end - t)
+    # not above dt_plain leaves the plain attempt min(dt_plain, t_end - t).
+    # The mixed form's update takes the step in FP32 (dt_plain is an FP32
+    # value already), so the step taken is that choice rounded to FP32.
     prop = np.minimum(raw, 16.0 * dt_plain)
-    want_step = np.where(raw > dt_plain, np.minimum(prop, rem), np.minimum(dt_plain, rem))
-    want_used = (raw > dt_plain) & (want_step > dt_plain)
+    want64 = np.where(raw > dt_plain, np.minimum(prop, rem), np.minimum(dt_plain, rem))
+    want_used = (raw > dt_plain) & (want64 > dt_plain)
+    want_step = want64.astype(np.float32).astype(np.float64)
+    assert np.array_equal(dt_plain, dt_plain.astype(np.float32).astype(np.float64))
     assert np.array_equal(step, want_step)
     assert np.array_equal(used.astype(bool), want_used)
     assert want_used.any() and (~want_used).any()
