@@ -38,7 +38,6 @@ N_ZONES = 4096
 WORKLOAD = "4096 zones x 150sp/1604rx, T9/rho profiles, t 1e-12 -> 1e-9 s"
 # the uneven-size batch: 2048 zones, 1:2:1, the chain over its own interval
 MIXED_ZONES = 2048
-MIXED_T_END = {"chain16_48": 1e-2, "net150_1604": 1e-9, "net365_4400": 1e-9}
 
 
 def _args():
@@ -600,24 +599,20 @@ def perfect_proposal(kn, g, dz, stream):
 def uneven_sizes(kn, stream, flush, n_sms, args):
     """2048 zones of the 16/48, 150/1604 and 365/4400 networks in the ratio
     1:2:1 (shuffled assignment, config-3 profiles; the chain over 1e-12 ->
-    1e-2 s, the others over 1e-12 -> 1e-9 s), all in one persistent launch
-    with the autotuned tiling."""
+    1e-2 s, the others over 1e-12 -> 1e-9 s: kn_inputs.uneven_batch), all in
+    one persistent launch with the autotuned tiling."""
     import torch
-    from kn_inputs import chain_network, mixed_assignment, net150, net365, profile_zones
-    nets = {"chain16_48": chain_network(), "net150_1604": net150(), "net365_4400": net365()}
-    lab = mixed_assignment(MIXED_ZONES, (1, 2, 1))
+    from kn_inputs import UNEVEN_T_END, uneven_batch
     dev = torch.device("cuda", torch.cuda.current_device())
     names = ("Y0", "T0", "rho0", "tau", "t_start", "t_end", "dt_trial")
-    gs, dzs, counts = [], [], {}
-    for k, (name, net) in enumerate(nets.items()):
-        idx = np.nonzero(lab == k)[0]
-        # zone z of the batch draws its profile from seed 1000 + z
-        z = profile_zones(net, MIXED_ZONES, t_end=MIXED_T_END[name]).subset(idx)
+    gs, dzs, counts, nets = [], [], {}, {}
+    for name, net, z, idx in uneven_batch(MIXED_ZONES):
         g = kn.Network(net)
         d = {n: torch.from_numpy(np.ascontiguousarray(getattr(z, n))).to(dev) for n in names}
         gs.append(g)
         dzs.append(d)
         counts[name] = int(len(idx))
+        nets[name] = net
 
     def set_all():
         for g, d in zip(gs, dzs):
@@ -635,7 +630,7 @@ def uneven_sizes(kn, stream, flush, n_sms, args):
         steps_all.append(r["steps"])
         per[name] = {"zones": counts[name], "zones_ok": st["zones_ok"], "accepted_steps": st["steps"],
                      "rejects": st["rejects"], "zones_per_s": st["zones_ok"] / (kms / 1e3),
-                     "zone_steps_per_s": st["steps"] / (kms / 1e3), "t_end": MIXED_T_END[name]}
+                     "zone_steps_per_s": st["steps"] / (kms / 1e3), "t_end": UNEVEN_T_END[name]}
         parts.append((net, st["steps"], st["rejects"]))
     roof = smem_roofline(parts, kms, tb["clocks"], n_sms)
     line = _form_line(tb, gs, MIXED_ZONES, roof, {"per_network": per, "tiling": tuned})

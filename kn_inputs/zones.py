@@ -88,3 +88,24 @@ def mixed_assignment(n_zones: int = 2048, ratio=(1, 2, 1), seed: int = 7) -> np.
         lab += [k] * c
     SplitMix64(seed).shuffle(lab)
     return np.asarray(lab, dtype=np.int32)
+
+
+# The uneven-size batch: the chain over its own interval (1e-12 -> 1e-2 s), the
+# 150- and 365-species networks over 1e-12 -> 1e-9 s.
+UNEVEN_T_END = {"chain16_48": 1e-2, "net150_1604": 1e-9, "net365_4400": 1e-9}
+
+
+def uneven_batch(n_zones: int = 2048, ratio=(1, 2, 1), seed: int = 7):
+    """The uneven-size batch: n_zones zones of the 16/48, 150/1604 and
+    365/4400 networks in `ratio`, shuffled (mixed_assignment); zone z of the
+    batch draws its profile from seed 1000 + z whatever its network.
+    Returns [(name, network, zones, batch indices)] in network order."""
+    from .networks import chain_network, net150, net365
+    lab = mixed_assignment(n_zones, ratio, seed)
+    out = []
+    for k, (name, net) in enumerate((("chain16_48", chain_network()), ("net150_1604", net150()),
+                                     ("net365_4400", net365()))):
+        idx = np.nonzero(lab == k)[0]
+        z = profile_zones(net, n_zones, t_end=UNEVEN_T_END[name]).subset(idx)
+        out.append((name, net, z, idx))
+    return out
