@@ -460,28 +460,39 @@ def other_forms(kn, g, net, zones, dz, stream, flush, mixed_line, args):
     def set_main():
         g.set_zones(dz, stream)
 
+    zns = torch.zeros((zones.n_zones, 2), dtype=torch.int64, device=torch.device("cuda", torch.cuda.current_device()))
+
+    def tail_of(tb, tuned):
+        groups = n_sms * (tuned["threads_per_cta"] // tuned["threads_per_zone"]) if tuned else None
+        return tail_stats(tb["zone_ns"], g.get(stream)["steps"], groups)
+
     out["mixed"] = {"median_rel_err_vs_tight_oracle": err(), "see": "the headline value and roofline"}
     # the split the measurement plan names: FP32 rates, fluxes and Kahan
     # gathers; FP64 update, conservation sum and test
     g.set_zones(dz, stream)
-    tuned = kn.autotune([g], kn.Opts(precision=kn.PREC_MIXED_FP64), max_steps=3000, stream=stream)
-    tb = timed_batches(kn, [g], set_main, kn.Opts(precision=kn.PREC_MIXED_FP64, use_graph=1), 3, 3, stream, flush)
+    # whole-batch trials: steady-state trials rank this FP64-pipe-bound form's
+    # tilings differently from the whole batch (measured: 4 x 160 against 2 x 160)
+    tuned = kn.autotune([g], kn.Opts(precision=kn.PREC_MIXED_FP64), max_steps=0, stream=stream)
+    tb = timed_batches(kn, [g], set_main, kn.Opts(precision=kn.PREC_MIXED_FP64, use_graph=1), 3, 3, stream, flush,
+                       zns)
     kms = _mean(tb["kernel_ms"])
     st = tb["stats"]
     roof = fp64_roofline(update_fp64_flops(net, st["steps"] + st["rejects"]), kms, fp64_peak,
                          "11 FP64 operations per species per attempt (update, conservation sum, test)")
     roof["smem"] = smem_roofline([(net, st["steps"], st["rejects"])], kms, tb["clocks"], n_sms)
     out["mixed_fp64_update"] = _form_line(tb, [g], zones.n_zones, roof,
-                                          {"median_rel_err_vs_tight_oracle": err(), "tiling": tuned})
+                                          {"median_rel_err_vs_tight_oracle": err(), "tiling": tuned,
+                                           "tail": tail_of(tb, tuned)})
     # every step in FP64
     g.set_zones(dz, stream)
     tuned = kn.autotune([g], kn.Opts(precision=kn.PREC_FP64), max_steps=100, stream=stream)
-    tb = timed_batches(kn, [g], set_main, kn.Opts(precision=kn.PREC_FP64, use_graph=1), 2, 1, stream, flush)
+    tb = timed_batches(kn, [g], set_main, kn.Opts(precision=kn.PREC_FP64, use_graph=1), 2, 1, stream, flush, zns)
     st = tb["stats"]
     roof = fp64_roofline(algorithmic_flops(net, st["steps"], st["rejects"]), _mean(tb["kernel_ms"]), fp64_peak,
                          "rates 5 R + fluxes 1/3/7 per 1/2/3-body reaction + gathers S_r + S_p per accepted step, "
                          "11 N per attempt")
-    out["fp64"] = _form_line(tb, [g], zones.n_zones, roof, {"median_rel_err_vs_tight_oracle": err(), "tiling": tuned})
+    out["fp64"] = _form_line(tb, [g], zones.n_zones, roof, {"median_rel_err_vs_tight_oracle": err(), "tiling": tuned,
+                                                            "tail": tail_of(tb, tuned)})
     # the learned proposal: records from training zones, training on the GPU,
     # then the batch with the network proposing and the plain test judging
     t0 = time.perf_counter()
@@ -496,7 +507,8 @@ def other_forms(kn, g, net, zones, dz, stream, flush, mixed_line, args):
     train_s = time.perf_counter() - t0
     g.set_zones(dz, stream)
     tuned = kn.autotune([g], kn.Opts(precision=kn.PREC_MIXED, mlp=mlp), max_steps=300, stream=stream)
-    tb = timed_batches(kn, [g], set_main, kn.Opts(precision=kn.PREC_MIXED, mlp=mlp, use_graph=1), 3, 3, stream, flush)
+    tb = timed_batches(kn, [g], set_main, kn.Opts(precision=kn.PREC_MIXED, mlp=mlp, use_graph=1), 3, 3, stream, flush,
+                       zns)
     st = tb["stats"]
     kms = _mean(tb["kernel_ms"])
     roof = smem_roofline([(net, st["steps"], st["rejects"])], kms, tb["clocks"], n_sms)
@@ -509,6 +521,7 @@ def other_forms(kn, g, net, zones, dz, stream, flush, mixed_line, args):
                              "peak_source": "derived: 128 FP32 FMA lanes/clk/SM x 2 x SMs x sampled clock"}
     out["mixed_learned"] = _form_line(tb, [g], zones.n_zones, roof, {
         "proposals_used": st["proposals_used"], "median_rel_err_vs_tight_oracle": err(), "tiling": tuned,
+        "tail": tail_of(tb, tuned),
         "records": int(feat.shape[0]), "record_gen_s": rec_s, "train_s": train_s,
         "train_kernel_s": train_kernel_s, "train_loss_first_last": [hist[0], hist[-1]]})
     out["learned_vs_plain_mixed_zones_per_s"] = out["mixed_learned"]["zones_per_s"] / mixed_line["zones_per_s"]
