@@ -1,0 +1,34 @@
+"""Host-side arithmetic of bench.py (no GPU): the per-zone tail statistics
+from timer stamps, and the roofline byte and flop counts against values
+worked by hand for a tiny network."""
+import numpy as np
+
+import bench
+from kn_inputs import custom_network
+
+
+def test_tail_stats_hand_worked():
+    # four zones: fetched at 0, 0, 5, 7 ms and written back at 10, 4, 6, 9 ms
+    ns = np.array([[0, 10], [0, 4], [5, 6], [7, 9]], dtype=np.int64) * 1_000_000 + 123
+    steps = np.array([1000, 400, 100, 200])
+    t = bench.tail_stats(ns, steps, groups=2)
+    assert t["span_ms"] == 10.0
+    assert t["queue_drained_ms"] == 7.0 and t["tail_ms"] == 3.0
+    assert t["longest_zone"] == {"ms": 10.0, "accepted_steps": 1000, "fetched_at_ms": 0.0, "us_per_step": 10.0}
+    # busy time 10 + 4 + 1 + 2 = 17 ms over 2 groups x 10 ms
+    assert abs(t["group_occupancy"] - 0.85) < 1e-12
+    assert t["finish_ms_p50_p90_p99_max"][-1] == 10.0
+
+
+def test_roofline_counts_hand_worked():
+    # a + b -> c (2-body), c -> a + b (1-body): R = 2, S_r = 3, S_p = 3, N = 3
+    net = custom_network([1.0, 1.0, 2.0], [((0, 1), (2,)), ((2,), (0, 1))], [0.0, 0.0], [0.0, 0.0])
+    s_r, s_p = net.slot_counts()
+    assert (s_r, s_p) == (3, 3)
+    # plan's figure per accepted step: 4 S_r + 4 (S_r + R) + 2 (S_r + S_p) + 4 S_p = 12 + 20 + 12 + 12
+    assert bench.algorithmic_smem_bytes(net, 10) == 10 * 56
+    # fuller count: 12 R + 8 S_r + 6 (S_r + S_p) + 8 N per step, 28 N per attempt
+    assert bench.full_smem_bytes(net, 10, 5) == 10 * (24 + 24 + 36 + 24) + 15 * 84
+    # FP64 flops: rates 5 R + fluxes 3 (2-body) + 1 (1-body) + gathers 6 per step, 11 N per attempt
+    assert bench.algorithmic_flops(net, 10, 5) == 10 * (10 + 4 + 6) + 15 * 33
+    assert bench.update_fp64_flops(net, 15) == 15 * 33
