@@ -500,6 +500,10 @@ def other_forms(kn, g, net, zones, dz, stream, flush, mixed_line, args):
             (chain_network(), profile_zones(chain_network(), 32, base_seed=600_000, t_end=1e-2))]
     feat, lab = learned.generate_records(jobs, 2_000_000, stream=stream)
     rec_s = time.perf_counter() - t0
+    # untimed warm-up on a slice: the first use of torch's shuffle, gather and
+    # reduction kernels in the process loads them (about 4 s on a fresh box)
+    learned.train_network(feat[:65536], lab[:65536], epochs=1, batch=4096, stream=stream)[0].close()
+    torch.cuda.synchronize()
     t0 = time.perf_counter()
     mlp, hist, train_kernel_s = learned.train_network(feat, lab, epochs=4, batch=4096, lr=1e-3, stream=stream,
                                                       time_kernels=True)
