@@ -327,6 +327,43 @@ def test_edge_cases(kn, oracle_mod):
     assert abs(r["steps"][0] - ref["steps"]) <= max(2, 0.02 * ref["steps"])
 
 
+@pytest.mark.parametrize("prec", [MIXED, M64])
+def test_edge_cases_fp32_flux_forms(kn, oracle_mod, prec):
+    """The limits and the clip to t_end in the FP32-flux forms, whose decision
+    code (FP32 step sizes in the mixed form) differs from the FP64 form's."""
+    net = net150()
+    g = kn.Network(net)
+    z = constant_zones(net, 3, t_end=1e-9)
+    g.set_zones(z)
+    kn.integrate_batch([g], kn.Opts(precision=prec, max_steps=50))
+    r = g.get()
+    assert (r["status"] == 1).all() and (r["steps"] == 50).all()
+    assert (r["t"] < z.t_end).all()
+    ref = oracle_mod.Oracle(net).integrate(z, 0, oracle_mod.OracleOpts(max_steps=50))
+    assert _rel_err(r["Y"][0], ref["Y"], 1e-10) < 10 * 0.05  # free-running tier
+    # every attempt rejected at once: MAX_REJECT after the first
+    g.set_zones(z)
+    kn.integrate_batch([g], kn.Opts(precision=prec, max_reject=0, grow_max=1e6, safety=1e6))
+    r = g.get()
+    assert (r["status"] == 4).all() and (r["rejects"] >= 1).all()
+    # a reject whose halved step falls below dt_min_frac * t: DT_UNDERFLOW
+    g.set_zones(z)
+    kn.integrate_batch([g], kn.Opts(precision=prec, dt_min_frac=0.9))
+    r = g.get()
+    ref = oracle_mod.Oracle(net).integrate(z, 0, oracle_mod.OracleOpts(dt_min_frac=0.9))
+    assert ref["status"] == 2 and (r["status"] == 2).all()
+    assert (r["rejects"] >= 1).all()
+    # an interval shorter than the trial dt: clipped to t_end, ending exactly there
+    z = constant_zones(net, 1, t_end=1e-12 + 1e-15)
+    g.set_zones(z)
+    kn.integrate_batch([g], kn.Opts(precision=prec))
+    r = g.get()
+    ref = oracle_mod.Oracle(net).integrate(z, 0)
+    assert r["status"][0] == 0 and r["t"][0] == z.t_end[0] == ref["t"]
+    assert abs(r["steps"][0] - ref["steps"]) <= max(2, 0.05 * ref["steps"])
+    g.close()
+
+
 def test_degenerate_networks(kn, oracle_mod):
     # a species touched by no reaction, an i -> i reaction, and identical reactants
     net = custom_network([1, 1, 2, 3], [((0,), (0,)), ((0, 0), (2,)), ((2,), (0, 0))],
