@@ -43,7 +43,7 @@ class _Net(C.Structure):
 class _Opts(C.Structure):
     _fields_ = [("kappa", C.c_double), ("eps_r", C.c_double), ("eps_c", C.c_double),
                 ("y_min", C.c_double), ("grow_max", C.c_double), ("safety", C.c_double),
-                ("shrink", C.c_double), ("max_reject", C.c_int32), ("pad", C.c_int32),
+                ("shrink", C.c_double), ("max_reject", C.c_int32), ("method", C.c_int32),
                 ("max_steps", C.c_int64), ("dt_min_frac", C.c_double)]
 
 
@@ -69,10 +69,14 @@ class OracleOpts:
     max_reject: int = 60
     max_steps: int = 10_000_000
     dt_min_frac: float = 1e-30
+    method: int = 0  # 0: Eq. (3) with the kappa switch; 1: alpha-QSS (METHOD_QSS)
 
     def c(self) -> _Opts:
         return _Opts(self.kappa, self.eps_r, self.eps_c, self.y_min, self.grow_max, self.safety,
-                     self.shrink, self.max_reject, 0, self.max_steps, self.dt_min_frac)
+                     self.shrink, self.max_reject, self.method, self.max_steps, self.dt_min_frac)
+
+
+METHOD_ASYMPTOTIC, METHOD_QSS = 0, 1
 
 
 _lib = None
@@ -108,6 +112,10 @@ def lib():
                                       C.POINTER(_Result), C.c_int]
         L.or_be_integrate_batch.argtypes = [C.POINTER(_Net), C.POINTER(_Opts), C.c_int32, P, P,
                                             P, C.c_int32, C.c_int32]
+        L.or_qss_alpha.argtypes = [C.c_double]
+        L.or_qss_alpha.restype = C.c_double
+        L.or_qss_predict.argtypes = [C.c_int, P, P, P, C.c_double, P]
+        L.or_qss_correct.argtypes = [C.c_int, P, P, P, P, P, C.c_double, P]
         L.or_lu_solve.argtypes = [C.c_int, P, P]
         L.or_lu_solve.restype = C.c_int
         _lib = L
@@ -178,6 +186,34 @@ class Oracle:
         k = self.rates(T9, rho)
         Fp, kk, _ = self.rhs(k, Y)
         return self.update(Y, Fp, kk, dt, kappa)
+
+    # ---- the alpha-QSS update (Sec. 11's alternative to Eq. 3) ----------
+    @staticmethod
+    def qss_alpha(x):
+        return lib().or_qss_alpha(float(x))
+
+    def qss_predict(self, Y, Fp, kk, dt):
+        Y, Fp, kk = _f64(Y), _f64(Fp), _f64(kk)
+        Yp = np.empty(self.N)
+        lib().or_qss_predict(self.N, _p(Y), _p(Fp), _p(kk), dt, _p(Yp))
+        return Yp
+
+    def qss_correct(self, Y, Fp0, k0, Fpp, kp, dt):
+        Y, Fp0, k0, Fpp, kp = map(_f64, (Y, Fp0, k0, Fpp, kp))
+        Yc = np.empty(self.N)
+        lib().or_qss_correct(self.N, _p(Y), _p(Fp0), _p(k0), _p(Fpp), _p(kp), dt, _p(Yc))
+        return Yc
+
+    def qss_step(self, Y, T9, rho, dt, T9p=None, rhop=None):
+        """One alpha-QSS step from Y: rates at (T9, rho) for the start state and
+        at (T9p, rhop) (default: the same) for the predicted one.  Returns
+        (Y', F+0, k0, Yp)."""
+        k = self.rates(T9, rho)
+        Fp0, k0, _ = self.rhs(k, Y)
+        Yp = self.qss_predict(Y, Fp0, k0, dt)
+        kq = k if T9p is None else self.rates(T9p, rhop)
+        Fpp, kp, _ = self.rhs(kq, Yp)
+        return self.qss_correct(Y, Fp0, k0, Fpp, kp, dt), Fp0, k0, Yp
 
     # ---- whole integrations --------------------------------------------
     @staticmethod

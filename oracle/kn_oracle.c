@@ -35,6 +35,11 @@
  *   or_integrate    the step loop: accept -> t += dt, grow dt by
  *                   min(grow_max, safety eps_r/rel, safety eps_c/cons);
  *                   reject -> dt *= shrink and retry from the same state.
+ *   or_qss_*        the explicit QSS update that Sec. 11 proposes as the
+ *                   alternative to Eq. (3); its formula is not in the paper,
+ *                   and the reading implemented is the alpha-QSS
+ *                   predictor-corrector of Mott, Oran & van Leer (2000), under
+ *                   the same accept test and step control (opts.method).
  *   or_be_*         backward Euler with Newton iterations and dense LU with
  *                   partial pivoting: the implicit comparison method of Sec. 7
  *                   (the paper's Xnet is sparse; dense is the brute-force form).
@@ -44,8 +49,12 @@
  * or_growth and a hand-worked run of the step loop (each case built so that a
  * plausible slip changes its outcome), the A<->B closed form, FE and
  * asymptotic linear maps against matrix powers, conservation of sum A_i Y_i,
- * equilibrium ratios of reversible pairs, positivity, rate scaling laws, and
- * backward Euler with Richardson extrapolation on tiny networks.
+ * equilibrium ratios of reversible pairs, positivity, rate scaling laws,
+ * backward Euler with Richardson extrapolation on tiny networks, and for the
+ * QSS update: alpha's Taylor series at x = 0 and limit at infinity, the
+ * single-step error of one linear decay against e^-x (O(x^7)), second-order
+ * convergence on a nonlinear network, and the trapezoidal rule for a
+ * species with no depletion.
  */
 #include <math.h>
 #include <stdint.h>
@@ -72,12 +81,13 @@ typedef struct {
     double safety;      /* safety factor on the ratio proposal */
     double shrink;      /* dt factor after a reject */
     int32_t max_reject; /* consecutive rejects before giving up */
-    int32_t pad;
+    int32_t method;     /* OR_ASYMPTOTIC: Eq. (3) with the kappa switch; OR_QSS: alpha-QSS */
     int64_t max_steps;  /* accepted steps before giving up */
     double dt_min_frac; /* dt < dt_min_frac * t is an underflow */
 } or_opts;
 
 enum { OR_OK = 0, OR_STEP_LIMIT = 1, OR_DT_UNDERFLOW = 2, OR_NONFINITE = 3, OR_MAX_REJECT = 4 };
+enum { OR_ASYMPTOTIC = 0, OR_QSS = 1 };
 
 void or_default_opts(or_opts *o)
 {
@@ -89,7 +99,7 @@ void or_default_opts(or_opts *o)
     o->safety = 0.9;
     o->shrink = 0.5;
     o->max_reject = 60;
-    o->pad = 0;
+    o->method = OR_ASYMPTOTIC;
     o->max_steps = 10000000;
     o->dt_min_frac = 1e-30;
 }
@@ -200,9 +210,88 @@ double or_growth(double rel, double cons, const or_opts *o)
     return g;
 }
 
+/* ---------------------------------------------------------------------------
+ * The explicit quasi-steady-state (QSS) update, the alternative to Eq. (3)
+ * that Sec. 11 proposes to try on the GPU.  The paper defers its formula to
+ * its QSS reference; the reading implemented is the alpha-QSS
+ * predictor-corrector of Mott, Oran & van Leer (J. Comput. Phys. 164 (2000)
+ * 407), the QSS scheme that reference applies, written in this file's
+ * notation: production F+_i and depletion rate k_i (F-_i = k_i Y_i).
+ *
+ * For dY/dt = F+ - k Y with F+ and k constant, the exact step is
+ *   Y(dt) = Y + dt (F+ - k Y) / (1 + alpha k dt),
+ *   alpha(x) = 1/(1 - e^-x) - 1/x,   x = k dt,
+ * and the scheme replaces alpha by its rational approximation in r = 1/x
+ *   alpha = (180 r^3 + 60 r^2 + 11 r + 1) / (360 r^3 + 60 r^2 + 12 r + 1),
+ * which tends to 1/2 as x -> 0 (the trapezoidal rule) and to 1 as x -> inf.
+ * ------------------------------------------------------------------------- */
+
+/* alpha as a function of x = k dt >= 0.  The same rational function is
+ * evaluated in powers of x for x <= 1 (multiplying through by x^3, so x = 0
+ * gives 1/2) and in powers of r = 1/x above, so neither form overflows. */
+double or_qss_alpha(double x)
+{
+    if (x <= 1.0)
+        return (180.0 + 60.0 * x + 11.0 * x * x + x * x * x) /
+               (360.0 + 60.0 * x + 12.0 * x * x + x * x * x);
+    double r = 1.0 / x;
+    return (180.0 * r * r * r + 60.0 * r * r + 11.0 * r + 1.0) /
+           (360.0 * r * r * r + 60.0 * r * r + 12.0 * r + 1.0);
+}
+
+/* Predictor: Yp_i = Y_i + dt (F+_i - k_i Y_i) / (1 + alpha(k_i dt) k_i dt),
+ * with F+ and k of the state Y at the start of the step. */
+void or_qss_predict(int N, const double *Y, const double *Fp, const double *kk, double dt,
+                    double *Yp)
+{
+    for (int i = 0; i < N; ++i) {
+        double x = kk[i] * dt;
+        double a = or_qss_alpha(x);
+        Yp[i] = Y[i] + dt * (Fp[i] - kk[i] * Y[i]) / (1.0 + a * x);
+    }
+}
+
+/* Corrector, from the start state (F+0, k0 of Y) and the predicted state
+ * (F+p, kp of Yp at t + dt):
+ *   kbar = (k0 + kp)/2,  abar = alpha(kbar dt),
+ *   F~   = abar F+p + (1 - abar) F+0,
+ *   Yc_i = Y_i + dt (F~_i - kbar_i Y_i) / (1 + abar kbar_i dt). */
+void or_qss_correct(int N, const double *Y, const double *Fp0, const double *k0,
+                    const double *Fpp, const double *kp, double dt, double *Yc)
+{
+    for (int i = 0; i < N; ++i) {
+        double kbar = 0.5 * (k0[i] + kp[i]);
+        double x = kbar * dt;
+        double a = or_qss_alpha(x);
+        double ft = a * Fpp[i] + (1.0 - a) * Fp0[i];
+        Yc[i] = Y[i] + dt * (ft - kbar * Y[i]) / (1.0 + a * x);
+    }
+}
+
 typedef struct {
     double T0, rho0, tau, t_start, t_end, dt_trial;
 } or_zone;
+
+/* One QSS trial step of length h from (Y, t), with F+0 and k0 already
+ * evaluated at (Y, t): the rates at t + h (recomputed only when the
+ * conditions vary), the right-hand side at the predicted state, then the
+ * corrector into Yn.  Work arrays: kr [R], Yp, Fpp, kp [N]. */
+static void qss_attempt(const or_net *n, const or_zone *z, double t, double h, const double *Y,
+                        const double *Fp0, const double *k0, const double *k_rates,
+                        double *kr, double *Yp, double *Fpp, double *kp, double *Yn)
+{
+    const int N = n->N;
+    or_qss_predict(N, Y, Fp0, k0, h, Yp);
+    const double *kq = k_rates;
+    if (z->tau > 0.0) {
+        double T9, rho;
+        or_conditions(z->T0, z->rho0, z->tau, t + h, &T9, &rho);
+        or_rates(n, T9, rho, kr);
+        kq = kr;
+    }
+    or_rhs(n, kq, Yp, Fpp, kp, NULL);
+    or_qss_correct(N, Y, Fp0, k0, Fpp, kp, h, Yn);
+}
 
 typedef struct {
     double t;          /* time reached */
@@ -226,6 +315,14 @@ void or_integrate(const or_net *n, const or_opts *o, const or_zone *z, double *Y
     double *Fp = (double *)malloc(sizeof(double) * (size_t)N);
     double *kk = (double *)malloc(sizeof(double) * (size_t)N);
     double *Yn = (double *)malloc(sizeof(double) * (size_t)N);
+    const int qss = o->method == OR_QSS;
+    double *kr = NULL, *Yp = NULL, *Fpp = NULL, *kp = NULL;
+    if (qss) {
+        kr = (double *)malloc(sizeof(double) * (size_t)R);
+        Yp = (double *)malloc(sizeof(double) * (size_t)N);
+        Fpp = (double *)malloc(sizeof(double) * (size_t)N);
+        kp = (double *)malloc(sizeof(double) * (size_t)N);
+    }
     double t = z->t_start, dt = z->dt_trial > 0.0 ? z->dt_trial : z->t_start;
     int64_t steps = 0, rejects = 0;
     int nrej = 0, status = OR_OK, rhs_valid = 0, last_finite = 1;
@@ -248,7 +345,10 @@ void or_integrate(const or_net *n, const or_opts *o, const or_zone *z, double *Y
         double rem = z->t_end - t;
         int clipped = dt >= rem;
         double h = clipped ? rem : dt;
-        or_update(N, Y, Fp, kk, h, o->kappa, Yn, NULL);
+        if (qss)
+            qss_attempt(n, z, t, h, Y, Fp, kk, k, kr, Yp, Fpp, kp, Yn);
+        else
+            or_update(N, Y, Fp, kk, h, o->kappa, Yn, NULL);
         double cons, rel;
         int finite;
         if (or_test(N, n->A, Y, Yn, o, &cons, &rel, &finite)) {
@@ -275,6 +375,7 @@ void or_integrate(const or_net *n, const or_opts *o, const or_zone *z, double *Y
     res->status = status;
     res->pad = 0;
     free(k); free(Fp); free(kk); free(Yn);
+    free(kr); free(Yp); free(Fpp); free(kp);
 }
 
 /* Replay: apply accepted steps with the given dt sequence, no tests. */
@@ -286,18 +387,30 @@ void or_replay(const or_net *n, const or_opts *o, const or_zone *z, double *Y,
     double *Fp = (double *)malloc(sizeof(double) * (size_t)N);
     double *kk = (double *)malloc(sizeof(double) * (size_t)N);
     double *Yn = (double *)malloc(sizeof(double) * (size_t)N);
+    const int qss = o->method == OR_QSS;
+    double *kr = NULL, *Yp = NULL, *Fpp = NULL, *kp = NULL;
+    if (qss) {
+        kr = (double *)malloc(sizeof(double) * (size_t)R);
+        Yp = (double *)malloc(sizeof(double) * (size_t)N);
+        Fpp = (double *)malloc(sizeof(double) * (size_t)N);
+        kp = (double *)malloc(sizeof(double) * (size_t)N);
+    }
     double t = z->t_start, T9, rho;
     for (int64_t s = 0; s < n_steps; ++s) {
         or_conditions(z->T0, z->rho0, z->tau, t, &T9, &rho);
         or_rates(n, T9, rho, k);
         or_rhs(n, k, Y, Fp, kk, NULL);
         double h = dts[s];
-        or_update(N, Y, Fp, kk, h, o->kappa, Yn, NULL);
+        if (qss)
+            qss_attempt(n, z, t, h, Y, Fp, kk, k, kr, Yp, Fpp, kp, Yn);
+        else
+            or_update(N, Y, Fp, kk, h, o->kappa, Yn, NULL);
         memcpy(Y, Yn, sizeof(double) * (size_t)N);
         t = (h >= z->t_end - t) ? z->t_end : t + h;
     }
     *t_out = t;
     free(k); free(Fp); free(kk); free(Yn);
+    free(kr); free(Yp); free(Fpp); free(kp);
 }
 
 /* Many zones, one thread each (OpenMP over zones when built with -fopenmp). */
