@@ -46,7 +46,7 @@ def _args():
     ap.add_argument("--steps", type=int, default=5)
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
-    ap.add_argument("--form", default="mixed", choices=["mixed", "mixed_fp64", "fp64"])
+    ap.add_argument("--form", default="mixed", choices=["mixed", "mixed_fp64", "fp64", "qss_fp64"])
     ap.add_argument("--zones", type=int, default=N_ZONES)
     ap.add_argument("--t-end", type=float, default=T_END, help="integration end time (s)")
     ap.add_argument("--strong", action="store_true",
@@ -147,6 +147,19 @@ def algorithmic_flops(net, steps, rejects):
     s_r, s_p = net.slot_counts()
     per_rx = np.where(nr == 1, 1, np.where(nr == 2, 3, 7)).sum()
     return float(steps * (5 * R + per_rx + s_r + s_p) + (steps + rejects) * 11 * net.n_species)
+
+
+def algorithmic_flops_qss(net, steps, rejects):
+    """Algorithmic FP64 operations of the alpha-QSS form per batch, counted as
+    in algorithmic_flops: per accepted step the new state's rates, fluxes and
+    gathers; per attempt the predicted state's rates, fluxes and gathers again,
+    and 49 per species (alpha 11 twice; the predictor 8 more; the corrector 13
+    more; the conservation sum and the relative test 6)."""
+    nr = net.n_reac
+    R = net.n_reactions
+    s_r, s_p = net.slot_counts()
+    per_state = 5 * R + np.where(nr == 1, 1, np.where(nr == 2, 3, 7)).sum() + s_r + s_p
+    return float(steps * per_state + (steps + rejects) * (per_state + 49 * net.n_species))
 
 
 def algorithmic_smem_bytes(net, steps):
@@ -493,6 +506,19 @@ def other_forms(kn, g, net, zones, dz, stream, flush, mixed_line, args):
                          "11 N per attempt")
     out["fp64"] = _form_line(tb, [g], zones.n_zones, roof, {"median_rel_err_vs_tight_oracle": err(), "tiling": tuned,
                                                             "tail": tail_of(tb, tuned)})
+    # the alpha-QSS update in FP64 (Sec. 11's question: does QSS in place of
+    # Eq. 3 integrate faster on the GPU?); the same accept test and controller
+    g.set_zones(dz, stream)
+    qo = dict(precision=kn.PREC_FP64, method=kn.METHOD_QSS)
+    tuned = kn.autotune([g], kn.Opts(**qo), max_steps=100, stream=stream)
+    tb = timed_batches(kn, [g], set_main, kn.Opts(**qo, use_graph=1), 1, 1, stream, flush, zns)
+    st = tb["stats"]
+    roof = fp64_roofline(algorithmic_flops_qss(net, st["steps"], st["rejects"]), _mean(tb["kernel_ms"]), fp64_peak,
+                         "rates 5 R + fluxes 1/3/7 per 1/2/3-body reaction + gathers S_r + S_p per accepted step "
+                         "and again per attempt (the predicted state), 49 N per attempt")
+    out["qss_fp64"] = _form_line(tb, [g], zones.n_zones, roof, {"median_rel_err_vs_tight_oracle": err(),
+                                                                "tiling": tuned, "tail": tail_of(tb, tuned)})
+    out["qss_vs_asymptotic_fp64_zones_per_s"] = out["qss_fp64"]["zones_per_s"] / out["fp64"]["zones_per_s"]
     # the learned proposal: records from training zones, training on the GPU,
     # then the batch with the network proposing and the plain test judging
     t0 = time.perf_counter()
@@ -710,15 +736,17 @@ def main():
     names = ("Y0", "T0", "rho0", "tau", "t_start", "t_end", "dt_trial")
     dz = {k: torch.from_numpy(np.ascontiguousarray(getattr(zones, k))).to(dev) for k in names}
     g = kn.Network(net)
-    prec = {"mixed": kn.PREC_MIXED, "mixed_fp64": kn.PREC_MIXED_FP64, "fp64": kn.PREC_FP64}[args.form]
+    prec = {"mixed": kn.PREC_MIXED, "mixed_fp64": kn.PREC_MIXED_FP64, "fp64": kn.PREC_FP64,
+            "qss_fp64": kn.PREC_FP64}[args.form]
+    method = kn.METHOD_QSS if args.form == "qss_fp64" else kn.METHOD_ASYMPTOTIC
     stream = torch.cuda.current_stream()
     tuned = None
     if not (args.tpz or args.tpc):
         # the project's autotuner picks the tiling on this batch (untimed
         # set-up; whole-batch trials, since the batch's tail matters here)
         g.set_zones(dz, stream)
-        tuned = kn.autotune([g], kn.Opts(precision=prec), max_steps=0, stream=stream)
-    opts = kn.Opts(precision=prec, use_graph=1, threads_per_zone=args.tpz, threads_per_cta=args.tpc)
+        tuned = kn.autotune([g], kn.Opts(precision=prec, method=method), max_steps=0, stream=stream)
+    opts = kn.Opts(precision=prec, method=method, use_graph=1, threads_per_zone=args.tpz, threads_per_cta=args.tpc)
     flush = torch.empty(256 * 1024 * 1024 // 4, dtype=torch.float32, device=dev)  # > L2 (129 MB)
 
     def set_main():
@@ -769,6 +797,11 @@ def main():
         roof = fp64_roofline(algorithmic_flops(net, st["steps"], st["rejects"]), kms, kn.measure_fp64_peak(stream),
                              "rates 5 R + fluxes 1/3/7 per 1/2/3-body reaction + gathers S_r + S_p per accepted "
                              "step, 11 N per attempt")
+    elif args.form == "qss_fp64":
+        roof = fp64_roofline(algorithmic_flops_qss(net, st["steps"], st["rejects"]), kms,
+                             kn.measure_fp64_peak(stream),
+                             "rates 5 R + fluxes 1/3/7 per 1/2/3-body reaction + gathers S_r + S_p per accepted "
+                             "step and again per attempt (the predicted state), 49 N per attempt")
     elif args.form == "mixed_fp64":
         # bound by the FP64 pipe (the update, the conservation sum and the
         # widening of F+ and k); the shared-memory figure rides along
@@ -801,7 +834,8 @@ def main():
         groups = n_sms * (tuned["threads_per_cta"] // tuned["threads_per_zone"])
     elif args.tpz and args.tpc:
         groups = n_sms * (args.tpc // args.tpz)
-    dtype = {"mixed": "f32 (float-float state)", "mixed_fp64": "f32 fluxes, f64 update", "fp64": "f64"}[args.form]
+    dtype = {"mixed": "f32 (float-float state)", "mixed_fp64": "f32 fluxes, f64 update", "fp64": "f64",
+             "qss_fp64": "f64"}[args.form]
     line = {"metric": METRIC, "value": value, "unit": "zone-steps/s", "n_gpus": world, "steps": args.steps,
             "warmup": max(3, args.warmup), "ms_per_step": ms / args.steps, "higher_is_better": True,
             "scaling": "strong" if args.strong else "weak", "vs_baseline": None, "dtype": dtype,

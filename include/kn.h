@@ -71,6 +71,11 @@ typedef enum {
                               error test in FP64 (FP64 abundances) */
 } kn_precision;
 
+typedef enum {
+    KN_METHOD_ASYMPTOTIC = 0, /* the kappa-switched update of Sec. 3, Eq. (3) */
+    KN_METHOD_QSS = 1         /* the alpha-QSS predictor-corrector (kn_opts.method) */
+} kn_method;
+
 /*
  * Network description (Sec. 2 and Sec. 6: the rate-library parameters that are
  * copied to the GPU once and stay resident).  Reaction j has 1..3 reactant
@@ -193,7 +198,25 @@ typedef struct {
        above it.  Its step count bounds what any learned proposal of this form
        can save.  0 = off. */
     int32_t follow_label;
-    int32_t pad_;
+    /* kn_method, default KN_METHOD_ASYMPTOTIC.  KN_METHOD_QSS replaces the
+       update of Eq. (3) by the explicit quasi-steady-state update that Sec. 11
+       proposes to try; the paper defers its formula to its QSS reference, and
+       the library takes the alpha-QSS predictor-corrector of Mott, Oran &
+       van Leer (J. Comput. Phys. 164 (2000) 407), with the production F+ and
+       the depletion rate k of Eq. (1):
+         alpha(x) = (180 r^3 + 60 r^2 + 11 r + 1) / (360 r^3 + 60 r^2 + 12 r + 1),
+                    r = 1/x
+         predictor  Yp = Y + dt (F+ - k Y) / (1 + alpha(k dt) k dt)
+                    (F+, k of Y at t)
+         corrector  kbar = (k + kp)/2, a = alpha(kbar dt),
+                    Y' = Y + dt (a F+p + (1 - a) F+ - kbar Y) / (1 + a kbar dt)
+                    (F+p, kp of Yp at t + dt)
+       and the same accept test and step control.  Each update
+       y + h (f - k y) / (1 + alpha k h) is evaluated in an algebraically equal
+       form without its cancellation at k h >> 1, which is non-negative for
+       non-negative inputs.  Each attempt evaluates the right-hand side twice.  Only with KN_PREC_FP64, and not combined with
+       mlp, record_features or follow_label (KN_ERR_INVALID_ARG otherwise). */
+    int32_t method;
     /* Per-zone timing (measurement): zone_ns [total zones][2] (device int64)
        receives the GPU global timer, in ns, when a zone group takes the zone
        from the work queue and when it has written the zone back.  Zones are

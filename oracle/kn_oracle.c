@@ -239,16 +239,57 @@ double or_qss_alpha(double x)
            (360.0 * r * r * r + 60.0 * r * r + 12.0 * r + 1.0);
 }
 
+/* 1 - alpha(x), from the same rational function: (D - N)/D with
+ * D - N = 180 + x^2 (powers of x) or 180 r^3 + r (powers of r), so that it
+ * keeps its relative accuracy as alpha -> 1. */
+static double qss_one_minus_alpha(double x)
+{
+    if (x <= 1.0)
+        return (180.0 + x * x) / (360.0 + 60.0 * x + 12.0 * x * x + x * x * x);
+    double r = 1.0 / x;
+    return (180.0 * r * r * r + r) / (360.0 * r * r * r + 60.0 * r * r + 12.0 * r + 1.0);
+}
+
+/* The scheme's update of one species, Y + dt (F - k Y) / (1 + alpha(x) x),
+ * x = k dt, with F the production term (F+ in the predictor, F~ in the
+ * corrector).  Written that way it is a difference of nearly equal terms
+ * once x >> 1 (Y and dt k Y / (1 + alpha x) are both about Y, the result
+ * about 12 Y / x^2 + F / k), and rounding leaves it a relative error of about
+ * eps x^2 / 12.  With alpha = N/D, 1 + alpha x = (D + x N)/D and
+ * 1 - (1 - alpha) x = (D - x (D - N))/D, so the same function is
+ *   (c0 Y + c1 dt F) / c2,
+ *   x <= 1:  c0 = D - x (D - N) = 360 - 120 x + 12 x^2,
+ *            c1 = D             = 360 + 60 x + 12 x^2 + x^3,
+ *            c2 = D + x N       = 360 + 240 x + 72 x^2 + 12 x^3 + x^4;
+ *   x > 1 (numerator and denominator divided by x^4, r = 1/x):
+ *            c0 = 360 r^4 - 120 r^3 + 12 r^2,
+ *            c1 = 360 r^4 + 60 r^3 + 12 r^2 + r,
+ *            c2 = 360 r^4 + 240 r^3 + 72 r^2 + 12 r + 1,
+ * a sum of non-negative terms: c0 = 12 (30 - 10 x + x^2) (or r^2 times it in
+ * r) has no real root, so Y, F >= 0 give a result >= 0. */
+static double qss_update1(double Y, double F, double k, double dt)
+{
+    double x = k * dt, c0, c1, c2;
+    if (x <= 1.0) {
+        c0 = 360.0 - 120.0 * x + 12.0 * x * x;
+        c1 = 360.0 + 60.0 * x + 12.0 * x * x + x * x * x;
+        c2 = 360.0 + 240.0 * x + 72.0 * x * x + 12.0 * x * x * x + x * x * x * x;
+    } else {
+        double r = 1.0 / x, r2 = r * r, r3 = r2 * r, r4 = r3 * r;
+        c0 = 360.0 * r4 - 120.0 * r3 + 12.0 * r2;
+        c1 = 360.0 * r4 + 60.0 * r3 + 12.0 * r2 + r;
+        c2 = 360.0 * r4 + 240.0 * r3 + 72.0 * r2 + 12.0 * r + 1.0;
+    }
+    return (c0 * Y + c1 * (dt * F)) / c2;
+}
+
 /* Predictor: Yp_i = Y_i + dt (F+_i - k_i Y_i) / (1 + alpha(k_i dt) k_i dt),
  * with F+ and k of the state Y at the start of the step. */
 void or_qss_predict(int N, const double *Y, const double *Fp, const double *kk, double dt,
                     double *Yp)
 {
-    for (int i = 0; i < N; ++i) {
-        double x = kk[i] * dt;
-        double a = or_qss_alpha(x);
-        Yp[i] = Y[i] + dt * (Fp[i] - kk[i] * Y[i]) / (1.0 + a * x);
-    }
+    for (int i = 0; i < N; ++i)
+        Yp[i] = qss_update1(Y[i], Fp[i], kk[i], dt);
 }
 
 /* Corrector, from the start state (F+0, k0 of Y) and the predicted state
@@ -262,9 +303,8 @@ void or_qss_correct(int N, const double *Y, const double *Fp0, const double *k0,
     for (int i = 0; i < N; ++i) {
         double kbar = 0.5 * (k0[i] + kp[i]);
         double x = kbar * dt;
-        double a = or_qss_alpha(x);
-        double ft = a * Fpp[i] + (1.0 - a) * Fp0[i];
-        Yc[i] = Y[i] + dt * (ft - kbar * Y[i]) / (1.0 + a * x);
+        double ft = or_qss_alpha(x) * Fpp[i] + qss_one_minus_alpha(x) * Fp0[i];
+        Yc[i] = qss_update1(Y[i], ft, kbar, dt);
     }
 }
 

@@ -69,7 +69,11 @@ static kn_status get_tables(kn_network* n, int prec, int Q, Tables** out) {
 // a zone group per SM, which is worth more than the saved rate evaluations.
 static bool rate_cache_on(const kn_network* n, int prec) { return prec != kPrecFP64 && 4 * n->R <= 8192; }
 
-static GroupLayout group_layout(const kn_network* n, int prec, int G, bool feat) {
+// Optional parts of a group's region: kLayoutFeat the learned proposal's and
+// the records' scratch, kLayoutQss the (F+, k) pairs of the QSS predicted state.
+enum { kLayoutFeat = 1, kLayoutQss = 2 };
+
+static GroupLayout group_layout(const kn_network* n, int prec, int G, int extras) {
     const int real = prec == kPrecFP64 ? 8 : 4;
     GroupLayout g{};
     int off = 0;
@@ -85,12 +89,14 @@ static GroupLayout group_layout(const kn_network* n, int prec, int G, bool feat)
     if (prec != kPrecFP64) off = pad16(off + 4 * 2 * (n->N + 1));
     g.off_Fk = off;
     off = pad16(off + real * 2 * n->N);
-    g.off_carry = off;
+    g.off_carry = off;  // directly after Fk: the tables' spare slot fk_span
     off = pad16(off + real);
+    g.off_Fk2 = off;    // the same span and spare slot again
+    if (extras & kLayoutQss) off = pad16(pad16(off + real * 2 * n->N) + real);
     g.off_red = off;
     off = pad16(off + (G / 32) * (8 * 3 + 4 + 4));
     g.off_feat = off;
-    if (feat) off = pad16(off + 4 * 384 + 4 * (3 * 64 + 4));
+    if (extras & kLayoutFeat) off = pad16(off + 4 * 384 + 4 * (3 * 64 + 4));
     g.off_state = off;
     off = pad16(off + (int)sizeof(GroupState));
     g.bytes = off;
@@ -138,7 +144,7 @@ static int base_group(const kn_network* n) {
 // For CTA size P, the tiling of one network: the smallest group size
 // G >= base_group that divides P with at most kMaxGroups groups, preferring
 // tables staged in shared memory; bytes = dynamic shared memory per CTA.
-static kn_status plan_tiling(kn_network* n, int prec, int P, int budget, int G_fixed, bool feat, Tiling& out,
+static kn_status plan_tiling(kn_network* n, int prec, int P, int budget, int G_fixed, int extras, Tiling& out,
                              bool& ok) {
     ok = false;
     Tiling best;
@@ -150,7 +156,7 @@ static kn_status plan_tiling(kn_network* n, int prec, int P, int budget, int G_f
         Tables* tb;
         kn_status s = get_tables(n, prec, G, &tb);
         if (s != KN_OK) return s;
-        const GroupLayout gl = group_layout(n, prec, G, feat);
+        const GroupLayout gl = group_layout(n, prec, G, extras);
         if (tb->tl.bytes + M * gl.bytes <= budget) {
             out = Tiling{G, M, 1, tb->tl.bytes + M * gl.bytes};
             ok = true;
@@ -351,6 +357,10 @@ static float rate_cache_tol(double cmax) {
     return cmax > 0.0 ? (float)(1.4901161193847656e-08 / (cmax * 0.6931471805599453)) : 3.0e38f;
 }
 
+// Which autotuned tiling a call uses: the plain form's, the learned form's or
+// the QSS form's (they differ in shared memory per group and in work per step).
+static int tuned_slot(const kn_opts* o, bool learn) { return learn ? 1 : (o->method == KN_METHOD_QSS ? 2 : 0); }
+
 static kn_status validate_opts(const kn_opts* o) {
     if (!o) return fail(KN_ERR_INVALID_ARG, "NULL opts");
     if (o->precision != KN_PREC_FP64 && o->precision != KN_PREC_MIXED && o->precision != KN_PREC_MIXED_FP64)
@@ -375,6 +385,10 @@ static kn_status validate_opts(const kn_opts* o) {
     }
     if (o->follow_label && !o->record_features)
         return fail(KN_ERR_INVALID_ARG, "opts.follow_label needs opts.record_features");
+    if (o->method != KN_METHOD_ASYMPTOTIC && o->method != KN_METHOD_QSS)
+        return fail(KN_ERR_INVALID_ARG, "opts.method must be KN_METHOD_ASYMPTOTIC or KN_METHOD_QSS");
+    if (o->method == KN_METHOD_QSS && (o->precision != KN_PREC_FP64 || o->mlp || o->record_features))
+        return fail(KN_ERR_INVALID_ARG, "opts.method KN_METHOD_QSS runs in KN_PREC_FP64 without mlp or records");
     if ((o->replay_dt != nullptr) != (o->replay_off != nullptr) ||
         (o->replay_dt != nullptr) != (o->replay_len != nullptr))
         return fail(KN_ERR_INVALID_ARG, "opts.replay_dt/off/len must be set together");
@@ -414,7 +428,7 @@ static kn_status prepare_launch(kn_network* const* nets, int n_nets, const kn_op
     const int prec = o->precision;
     const bool learn = o->mlp != nullptr && !probe;
     const bool record = o->record_features != nullptr && !probe;
-    const bool feat = learn || record;
+    const int extras = (learn || record ? kLayoutFeat : 0) | (o->method == KN_METHOD_QSS ? kLayoutQss : 0);
     // the staged network takes the front of the CTA's shared memory
     const int budget = di.smem_optin - 1024 - 64 - (learn ? kMlpSmemBytes : 0);
     memset(&lp, 0, sizeof lp);
@@ -430,14 +444,14 @@ static kn_status prepare_launch(kn_network* const* nets, int n_nets, const kn_op
         else if (o->threads_per_zone) P_lo = P_hi = o->threads_per_zone;
         // an autotuned tiling (kn_autotune) when the caller gives none
         if (!o->threads_per_cta && !o->threads_per_zone) {
-            const int tP = nets[0]->tuned_P[prec][learn ? 1 : 0];
+            const int tP = nets[0]->tuned_P[prec][tuned_slot(o, learn)];
             bool all = tP > 0;
             Tiling cand[kMaxPlans];
             for (int p = 0; p < n_nets && all; ++p) {
-                const int tG = nets[p]->tuned_G[prec][learn ? 1 : 0];
+                const int tG = nets[p]->tuned_G[prec][tuned_slot(o, learn)];
                 bool ok = false;
-                all = nets[p]->tuned_P[prec][learn ? 1 : 0] == tP && tG > 0;
-                if (all && (s = plan_tiling(nets[p], prec, tP, budget, tG, feat, cand[p], ok)) != KN_OK) return s;
+                all = nets[p]->tuned_P[prec][tuned_slot(o, learn)] == tP && tG > 0;
+                if (all && (s = plan_tiling(nets[p], prec, tP, budget, tG, extras, cand[p], ok)) != KN_OK) return s;
                 all = all && ok;
             }
             if (all) {
@@ -463,7 +477,7 @@ static kn_status prepare_launch(kn_network* const* nets, int n_nets, const kn_op
             for (int G = g0; G <= g1; G += 32) {
                 Tables* tb;
                 if ((s = get_tables(n, prec, G, &tb)) != KN_OK) return s;
-                const GroupLayout gl = group_layout(n, prec, G, feat);
+                const GroupLayout gl = group_layout(n, prec, G, extras);
                 int M = std::min(kMaxGroups, 1024 / G);
                 if (!small) M = std::min(M, kTargetGroups);
                 while (M > 0 && tb->tl.bytes + M * gl.bytes > budget) --M;
@@ -482,7 +496,7 @@ static kn_status prepare_launch(kn_network* const* nets, int n_nets, const kn_op
                 Tiling cand[kMaxPlans];
                 for (int p = 0; p < n_nets && all; ++p) {
                     bool ok;
-                    if ((s = plan_tiling(nets[p], prec, P, budget, o->threads_per_zone, feat, cand[p], ok)) != KN_OK)
+                    if ((s = plan_tiling(nets[p], prec, P, budget, o->threads_per_zone, extras, cand[p], ok)) != KN_OK)
                         return s;
                     all = ok;
                     all_smem = all_smem && ok && cand[p].smem_tables;
@@ -504,7 +518,7 @@ static kn_status prepare_launch(kn_network* const* nets, int n_nets, const kn_op
         const Tiling t = tl[p];
         Tables* tb;
         if ((s = get_tables(n, prec, t.G, &tb)) != KN_OK) return s;
-        const GroupLayout gl = group_layout(n, prec, t.G, feat);
+        const GroupLayout gl = group_layout(n, prec, t.G, extras);
         PlanDev& P = lp.plans[p];
         P.blob = (const unsigned char*)tb->blob->p;
         P.tl = tb->tl;
@@ -586,6 +600,7 @@ static kn_status prepare_launch(kn_network* const* nets, int n_nets, const kn_op
     D.max_steps = o->max_steps;
     D.max_reject = o->max_reject;
     D.lockstep = o->lockstep;
+    D.method = o->method;
     set_guard_band(D, o);
     D.zone_ns = probe ? nullptr : (long long*)o->zone_ns;
     D.replay_dt = o->replay_dt;
@@ -781,7 +796,7 @@ kn_status noalloc_prepare(kn_network* n, const kn_opts* o, int32_t n_zones, cons
     const Tables& tb = it->second;
     const int budget = di.smem_optin - 1024 - 64;
     const int M = P / G;
-    const GroupLayout gl = group_layout(n, o->precision, G, false);
+    const GroupLayout gl = group_layout(n, o->precision, G, o->method == KN_METHOD_QSS ? kLayoutQss : 0);
     int smem_tables = tb.tl.bytes + M * gl.bytes <= budget;
     const int bytes = (smem_tables ? tb.tl.bytes : 0) + M * gl.bytes;
     if (bytes > budget) return fail(KN_ERR_INVALID_ARG, "kn_integrate_noalloc: tiling needs %d B of shared memory", bytes);
@@ -840,6 +855,7 @@ kn_status noalloc_prepare(kn_network* n, const kn_opts* o, int32_t n_zones, cons
     D.dt_min_frac = o->dt_min_frac;
     D.max_steps = o->max_steps;
     D.max_reject = o->max_reject;
+    D.method = o->method;
     set_guard_band(D, o);
     nbar = n->nbar;
     rbar = n->rbar;
@@ -856,7 +872,7 @@ cudaError_t launch_fp64_peak(double* out, int blocks, int threads, int iters, cu
 
 namespace {
 // Candidate (P, G) tilings for the listed networks.
-static kn_status tiling_candidates(kn_network* const* nets, int n_nets, int prec, bool feat, int budget,
+static kn_status tiling_candidates(kn_network* const* nets, int n_nets, int prec, int extras, int budget,
                                    std::vector<std::pair<int, int>>& out) {
     kn_status s;
     if (n_nets == 1) {
@@ -864,7 +880,7 @@ static kn_status tiling_candidates(kn_network* const* nets, int n_nets, int prec
         for (int G = base_group(n); G <= 512; G += 32) {
             Tables* tb;
             if ((s = get_tables(n, prec, G, &tb)) != KN_OK) return s;
-            const GroupLayout gl = group_layout(n, prec, G, feat);
+            const GroupLayout gl = group_layout(n, prec, G, extras);
             int M = std::min(kMaxGroups, 1024 / G);
             while (M > 0 && tb->tl.bytes + M * gl.bytes > budget) --M;
             if (M == 0) {  // tables in global memory
@@ -928,7 +944,8 @@ kn_status kn_autotune(kn_network* const* nets, int32_t n_nets, const kn_opts* o,
     const bool learn = o->mlp != nullptr;
     const int budget = di.smem_optin - 1024 - 64 - (learn ? kMlpSmemBytes : 0);
     std::vector<std::pair<int, int>> cands;
-    if ((s = tiling_candidates(nets, n_nets, prec, learn, budget, cands)) != KN_OK) return s;
+    const int extras = (learn ? kLayoutFeat : 0) | (o->method == KN_METHOD_QSS ? kLayoutQss : 0);
+    if ((s = tiling_candidates(nets, n_nets, prec, extras, budget, cands)) != KN_OK) return s;
     // save the zone abundances (the trials integrate in place)
     std::vector<std::unique_ptr<DevBuf>> saved(n_nets);
     for (int p = 0; p < n_nets; ++p) {
@@ -1016,12 +1033,12 @@ kn_status kn_autotune(kn_network* const* nets, int32_t n_nets, const kn_opts* o,
         if (G == 0) {
             Tiling tlp;
             bool ok = false;
-            if ((s = plan_tiling(nets[p], prec, win.threads_per_cta, budget, 0, learn, tlp, ok)) != KN_OK) return s;
+            if ((s = plan_tiling(nets[p], prec, win.threads_per_cta, budget, 0, extras, tlp, ok)) != KN_OK) return s;
             if (!ok) return fail(KN_ERR_STATE, "kn_autotune: winning tiling no longer fits");
             G = tlp.G;
         }
-        nets[p]->tuned_P[prec][learn ? 1 : 0] = win.threads_per_cta;
-        nets[p]->tuned_G[prec][learn ? 1 : 0] = G;
+        nets[p]->tuned_P[prec][tuned_slot(o, learn)] = win.threads_per_cta;
+        nets[p]->tuned_G[prec][tuned_slot(o, learn)] = G;
     }
     *best = win;
     return KN_OK;

@@ -76,8 +76,8 @@ struct kn_network {
     bool has_const = true;  // conservative until zones are known
     bool zones_set = false;
     int trial_Z = 0;        // > 0 during autotune trials: integrate only the first trial_Z zones of the queue
-    int tuned_P[3][2] = {};  // [precision][learned form]: autotuned CTA size
-    int tuned_G[3][2] = {};  // ... and zone group size
+    int tuned_P[3][3] = {};  // [precision][plain, learned, QSS]: autotuned CTA size
+    int tuned_G[3][3] = {};  // ... and zone group size
 };
 
 namespace kn {

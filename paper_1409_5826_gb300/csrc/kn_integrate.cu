@@ -150,6 +150,7 @@ struct GroupPtrs {
     float* Ylo;   // mixed form: low parts of the float-float abundances (high parts: Y32)
     float* Y32;
     void* Fk;
+    void* Fk2;  // QSS: (F+, k) pairs of the predicted state
     double* red_c;
     double* red_n;
     double* red_d;
@@ -159,13 +160,87 @@ struct GroupPtrs {
     int* hist;    // [3][64] + [4] counters
 };
 
-// (d) kappa-switched update (Sec. 3, Eq. 3) with step h from buffer cur into
-// nxt, and each warp's share of the error measures (no barrier inside).
-// FP64 form: every step in FP64, in the order of the definitions.
+// ---------------------------------------------------------------------------
+// The explicit quasi-steady-state update (Sec. 11 proposes it as the
+// alternative to Eq. 3; its formula is the alpha-QSS predictor-corrector of
+// Mott, Oran & van Leer, J. Comput. Phys. 164 (2000) 407).  FP64 form only.
+// ---------------------------------------------------------------------------
+
+// alpha(x), x = k dt >= 0, is the rational approximation
+// N/D = (180 r^3 + 60 r^2 + 11 r + 1) / (360 r^3 + 60 r^2 + 12 r + 1), r = 1/x,
+// of 1/(1 - e^-x) - 1/x, the alpha that makes the step exact for constant F+
+// and k.  The corrector's weights a = alpha and b = 1 - alpha = (D - N)/D,
+// with D - N = 180 r^3 + r, so that b keeps its relative accuracy as
+// alpha -> 1.  Horner forms in x up to x = 1 (numerators and denominator
+// times x^3), in r above, so nothing overflows and x = 0 gives 1/2, 1/2.
+__device__ __forceinline__ void qss_weights(double x, double& a, double& b) {
+    double n, d, dn;
+    if (x <= 1.0) {
+        n = fma(fma(x + 11.0, x, 60.0), x, 180.0);
+        d = fma(fma(x + 12.0, x, 60.0), x, 360.0);
+        dn = fma(x, x, 180.0);
+    } else {
+        const double r = 1.0 / x;
+        n = fma(fma(fma(180.0, r, 60.0), r, 11.0), r, 1.0);
+        d = fma(fma(fma(360.0, r, 60.0), r, 12.0), r, 1.0);
+        dn = r * fma(180.0 * r, r, 1.0);
+    }
+    const double inv = 1.0 / d;
+    a = n * inv;
+    b = dn * inv;
+}
+
+// The scheme's update of one species, y + h (f - k y) / (1 + alpha(k h) k h),
+// with f the production term (F+ in the predictor, the corrector's blend).
+// As printed it is a difference of nearly equal terms once k h >> 1 (the
+// result is about 12 y / (k h)^2 + f / k), which rounding would leave with a
+// relative error of about eps (k h)^2 / 12; the same function is evaluated as
+// (c0 y + c1 h f) / c2 from 1 + alpha x = (D + x N)/D and
+// 1 - (1 - alpha) x = (D - x (D - N))/D, x = k h:
+//   x <= 1: c0 = 12 x^2 - 120 x + 360, c1 = x^3 + 12 x^2 + 60 x + 360,
+//           c2 = x^4 + 12 x^3 + 72 x^2 + 240 x + 360;
+//   x > 1 (divided through by x^4, r = 1/x): c0 = r^2 (360 r^2 - 120 r + 12),
+//           c1 = r (360 r^3 + 60 r^2 + 12 r + 1), c2 = 360 r^4 + 240 r^3 + 72 r^2 + 12 r + 1.
+// c0 > 0 for every x, so y, f >= 0 give a result >= 0.
+__device__ __forceinline__ double qss_update1(double y, double f, double k, double h) {
+    const double x = k * h;
+    double c0, c1, c2;
+    if (x <= 1.0) {
+        c0 = fma(fma(12.0, x, -120.0), x, 360.0);
+        c1 = fma(fma(x + 12.0, x, 60.0), x, 360.0);
+        c2 = fma(fma(fma(x + 12.0, x, 72.0), x, 240.0), x, 360.0);
+    } else {
+        const double r = 1.0 / x;
+        c0 = fma(fma(360.0, r, -120.0), r, 12.0) * (r * r);
+        c1 = fma(fma(fma(360.0, r, 60.0), r, 12.0), r, 1.0) * r;
+        c2 = fma(fma(fma(fma(360.0, r, 240.0), r, 72.0), r, 12.0), r, 1.0);
+    }
+    return fma(c0, y, c1 * (h * f)) / c2;
+}
+
+// Predictor: Yp = Y + h (F+ - k Y) / (1 + alpha(k h) k h) from buffer cur into
+// nxt, with (F+, k) of the current state.  No barrier inside.
+__device__ __forceinline__ void qss_predict(const PlanDev& P, const GroupPtrs& g, int lane, int cur, double h) {
+    const int N = P.N, G = P.G, NP1 = N + 1;
+    const double* Fk = (const double*)g.Fk;
+    const double* Yc = g.Y64 + cur * NP1;
+    double* Yp = g.Y64 + (cur ^ 1) * NP1;
+    for (int i = lane; i < N; i += G) Yp[i] = qss_update1(Yc[i], Fk[2 * i], Fk[2 * i + 1], h);
+}
+
+// (d) the update with step h from buffer cur into nxt, and each warp's share
+// of the error measures (no barrier inside).  FP64 form: every step in FP64,
+// in the order of the definitions.  QSS = false: the kappa-switched update
+// (Sec. 3, Eq. 3).  QSS = true: the alpha-QSS corrector from the current
+// state's (F+, k) and the predicted state's (F+p, kp) in Fk2:
+//   kbar = (k + kp)/2, a = alpha(kbar h),
+//   Y' = Y + h (a F+p + (1 - a) F+ - kbar Y) / (1 + a kbar h).
+template <bool QSS>
 __device__ __forceinline__ void update_reduce_fp64(const PlanDev& P, const OptsDev& O, const GroupPtrs& g, int lane,
                                                    int cur, double h, int z) {
     const int N = P.N, G = P.G, NP1 = N + 1;
     const double* Fk = (const double*)g.Fk;
+    const double* Fk2 = (const double*)g.Fk2;
     const double* A = (const double*)g.A;
     const double* Yc = g.Y64 + cur * NP1;
     double* Yn64 = g.Y64 + (cur ^ 1) * NP1;
@@ -173,8 +248,16 @@ __device__ __forceinline__ void update_reduce_fp64(const PlanDev& P, const OptsD
     double csum = 0.0, bn = 0.0, bd = 1.0;
     for (int i = lane; i < N; i += G) {
         const double y = Yc[i], fp = Fk[2 * i], kk = Fk[2 * i + 1];
-        const double kdt = kk * h;
-        const double yn = (kdt >= kappa) ? (y + h * fp) / (1.0 + kdt) : y + h * (fp - kk * y);
+        double yn;
+        if (QSS) {
+            const double kbar = 0.5 * (kk + Fk2[2 * i + 1]);
+            double a, b;
+            qss_weights(kbar * h, a, b);
+            yn = qss_update1(y, fma(a, Fk2[2 * i], b * fp), kbar, h);
+        } else {
+            const double kdt = kk * h;
+            yn = (kdt >= kappa) ? (y + h * fp) / (1.0 + kdt) : y + h * (fp - kk * y);
+        }
         Yn64[i] = yn;
         const double d = yn - y;
         csum = fma(A[i], d, csum);
@@ -393,8 +476,9 @@ __device__ __forceinline__ void update_reduce_mixed64(const PlanDev& P, const Op
     }
 }
 
-// h: the step (FP64 forms); h32: the same step in FP32 (the mixed form's update)
-template <int PREC>
+// h: the step (FP64 forms); h32: the same step in FP32 (the mixed form's update);
+// QSS: the alpha-QSS corrector instead of Eq. 3 (FP64 form)
+template <int PREC, bool QSS = false>
 __device__ __forceinline__ void update_reduce(const PlanDev& P, const OptsDev& O, const GroupPtrs& g, int lane,
                                               int cur, double h, float h32, int z) {
     if (PREC == kPrecMixed)
@@ -402,7 +486,7 @@ __device__ __forceinline__ void update_reduce(const PlanDev& P, const OptsDev& O
     else if (PREC == kPrecMixed64)
         update_reduce_mixed64(P, O, g, lane, cur, h, z);
     else
-        update_reduce_fp64(P, O, g, lane, cur, h, z);
+        update_reduce_fp64<QSS>(P, O, g, lane, cur, h, z);
 }
 
 // lane 0, after the barrier that follows update_reduce: combine the warps.
@@ -762,7 +846,86 @@ __device__ __forceinline__ void flux_pass(const PlanDev& P, const GroupPtrs& g, 
     }
 }
 
-template <int PREC, bool FEAT>
+// (b) sliced gathers of the row sums F+_i and k_i into the (F+, k) pairs at
+// Fb: warp w sums its slices, one row piece per lane; the pieces of a split
+// row (consecutive lanes, same destination) are added by a segmented
+// reduction into the first one.  FP64 form: FP64 sums.  Mixed form: plain
+// FP32 sums -- every term of a row is positive, so a row of k pieces of at
+// most L terms is within (L - 1 + ceil(log2 k)) 2^-24 of its value, relative.
+// Mixed form with the FP64 update: Kahan-compensated FP32 sums, and the
+// pieces' (sum, compensation) pairs added with TwoSum.  Padding lanes store
+// to the spare slot after the pairs.  No barrier inside.
+template <int PREC>
+__device__ __forceinline__ void gather_pass(const PlanDev& P, const GroupPtrs& g, int lane, unsigned char* Fb_) {
+    using real = typename PrecTraits<PREC>::real;
+    const real* V = (const real*)g.V;
+    const int w = lane >> 5, l = lane & 31;
+    const int s1 = g.wsl[w + 1];
+    const bool boff = P.tl.sidx_bytes != 0;
+    unsigned char* __restrict__ Fb = Fb_;
+    const real* __restrict__ Vr = V;
+    for (int sl = g.wsl[w]; sl < s1; ++sl) {
+        const uint2 hd = g.shdr[sl];
+        const uint16_t* __restrict__ ix = g.sidx + hd.x + l;
+        const int len = (int)(hd.y & 0x7fffffffu);
+        const unsigned int d = g.sdst[32 * sl + l];
+        if (PREC == kPrecMixed64) {
+            AccKahan ak;
+            ak.reset();
+            if (boff) {
+                const unsigned char* __restrict__ Vb = (const unsigned char*)Vr;
+#pragma unroll 4
+                for (int k = 0; k < len; ++k) ak.add((float)*(const real*)(Vb + ix[32 * k]));
+            } else {
+#pragma unroll 4
+                for (int k = 0; k < len; ++k) ak.add((float)Vr[ix[32 * k]]);
+            }
+            float hi = ak.s, lo = -ak.c;
+            bool first = true;
+            if (hd.y >> 31) {  // warp-uniform
+#pragma unroll
+                for (int off = 1; off < 32; off <<= 1) {
+                    const float oh = __shfl_down_sync(0xffffffffu, hi, off);
+                    const float ol = __shfl_down_sync(0xffffffffu, lo, off);
+                    const unsigned int od = __shfl_down_sync(0xffffffffu, d, off);
+                    if (l + off < 32 && od == d) {
+                        float s2, e2;
+                        two_sum(hi, oh, s2, e2);
+                        hi = s2;
+                        lo = __fadd_rn(__fadd_rn(lo, ol), e2);
+                    }
+                }
+                const unsigned int ud = __shfl_up_sync(0xffffffffu, d, 1);
+                first = l == 0 || ud != d;
+            }
+            if (first) *(real*)(Fb + d) = (real)__fadd_rn(hi, lo);
+            continue;
+        }
+        real acc = (real)0;
+        if (boff) {  // byte offsets into V (uniform per table)
+            const unsigned char* __restrict__ Vb = (const unsigned char*)Vr;
+#pragma unroll 4
+            for (int k = 0; k < len; ++k) acc = acc + *(const real*)(Vb + ix[32 * k]);
+        } else {
+#pragma unroll 4
+            for (int k = 0; k < len; ++k) acc = acc + Vr[ix[32 * k]];
+        }
+        bool first = true;
+        if (hd.y >> 31) {  // warp-uniform
+#pragma unroll
+            for (int off = 1; off < 32; off <<= 1) {
+                const real o = __shfl_down_sync(0xffffffffu, acc, off);
+                const unsigned int od = __shfl_down_sync(0xffffffffu, d, off);
+                if (l + off < 32 && od == d) acc = acc + o;
+            }
+            const unsigned int ud = __shfl_up_sync(0xffffffffu, d, 1);
+            first = l == 0 || ud != d;
+        }
+        if (first) *(real*)(Fb + d) = acc;
+    }
+}
+
+template <int PREC, bool FEAT, bool QSS>
 __device__ void run_group(const PlanDev& P, const OptsDev& O, const unsigned char* tb, const unsigned char* mlp_smem,
                           unsigned char* gbase, const int lane, const GroupSync gs) {
     using real = typename PrecTraits<PREC>::real;
@@ -786,6 +949,7 @@ __device__ void run_group(const PlanDev& P, const OptsDev& O, const unsigned cha
     g.Ylo = (float*)(gbase + P.gl.off_Y);
     g.Y32 = (float*)(gbase + P.gl.off_Y32);
     g.Fk = gbase + P.gl.off_Fk;
+    g.Fk2 = gbase + P.gl.off_Fk2;
     {
         const int nw = G >> 5;
         g.red_c = (double*)(gbase + P.gl.off_red);
@@ -861,6 +1025,8 @@ __device__ void run_group(const PlanDev& P, const OptsDev& O, const unsigned cha
                 S.u_scale = S.constant ? 0.f : __double2float_rn(S.inv_tau * 1.4426950408889634);
                 S.s = 0.0;
                 S.poly = 0;
+                S.s_p = 0.0;
+                S.poly_p = 0;
                 S.u = 0.f;
                 S.u_ref = -1e30f;  // the first flux pass computes the cached rates
                 S.steps = 0;
@@ -931,81 +1097,8 @@ __device__ void run_group(const PlanDev& P, const OptsDev& O, const unsigned cha
                     gs.sync();
                     if (lane == 0 && refresh) S.u_ref = S.u;
                 }
-                // (b) sliced gathers: warp w sums its slices, one row piece per
-                //     lane; the pieces of a split row (consecutive lanes, same
-                //     destination) are added by a segmented reduction into
-                //     the first one.  FP64 form: FP64 sums.  Mixed form: plain
-                //     FP32 sums -- every term of a row is positive, so a row of
-                //     k pieces of at most L terms is within (L - 1 + ceil(log2 k))
-                //     2^-24 of its value, relative.  Mixed form with the FP64
-                //     update: Kahan-compensated FP32 sums, and the pieces'
-                //     (sum, compensation) pairs added with TwoSum.
-                {
-                    const int w = lane >> 5, l = lane & 31;
-                    const int s1 = g.wsl[w + 1];
-                    const bool boff = P.tl.sidx_bytes != 0;
-                    unsigned char* __restrict__ Fb = (unsigned char*)Fk;
-                    const real* __restrict__ Vr = V;
-                    for (int sl = g.wsl[w]; sl < s1; ++sl) {
-                        const uint2 hd = g.shdr[sl];
-                        const uint16_t* __restrict__ ix = g.sidx + hd.x + l;
-                        const int len = (int)(hd.y & 0x7fffffffu);
-                        const unsigned int d = g.sdst[32 * sl + l];
-                        if (PREC == kPrecMixed64) {
-                            AccKahan ak;
-                            ak.reset();
-                            if (boff) {
-                                const unsigned char* __restrict__ Vb = (const unsigned char*)Vr;
-#pragma unroll 4
-                                for (int k = 0; k < len; ++k) ak.add((float)*(const real*)(Vb + ix[32 * k]));
-                            } else {
-#pragma unroll 4
-                                for (int k = 0; k < len; ++k) ak.add((float)Vr[ix[32 * k]]);
-                            }
-                            float hi = ak.s, lo = -ak.c;
-                            bool first = true;
-                            if (hd.y >> 31) {  // warp-uniform
-#pragma unroll
-                                for (int off = 1; off < 32; off <<= 1) {
-                                    const float oh = __shfl_down_sync(0xffffffffu, hi, off);
-                                    const float ol = __shfl_down_sync(0xffffffffu, lo, off);
-                                    const unsigned int od = __shfl_down_sync(0xffffffffu, d, off);
-                                    if (l + off < 32 && od == d) {
-                                        float s2, e2;
-                                        two_sum(hi, oh, s2, e2);
-                                        hi = s2;
-                                        lo = __fadd_rn(__fadd_rn(lo, ol), e2);
-                                    }
-                                }
-                                const unsigned int ud = __shfl_up_sync(0xffffffffu, d, 1);
-                                first = l == 0 || ud != d;
-                            }
-                            if (first) *(real*)(Fb + d) = (real)__fadd_rn(hi, lo);
-                            continue;
-                        }
-                        real acc = (real)0;
-                        if (boff) {  // byte offsets into V (uniform per table)
-                            const unsigned char* __restrict__ Vb = (const unsigned char*)Vr;
-#pragma unroll 4
-                            for (int k = 0; k < len; ++k) acc = acc + *(const real*)(Vb + ix[32 * k]);
-                        } else {
-#pragma unroll 4
-                            for (int k = 0; k < len; ++k) acc = acc + Vr[ix[32 * k]];
-                        }
-                        bool first = true;
-                        if (hd.y >> 31) {  // warp-uniform
-#pragma unroll
-                            for (int off = 1; off < 32; off <<= 1) {
-                                const real o = __shfl_down_sync(0xffffffffu, acc, off);
-                                const unsigned int od = __shfl_down_sync(0xffffffffu, d, off);
-                                if (l + off < 32 && od == d) acc = acc + o;
-                            }
-                            const unsigned int ud = __shfl_up_sync(0xffffffffu, d, 1);
-                            first = l == 0 || ud != d;
-                        }
-                        if (first) *(real*)(Fb + d) = acc;
-                    }
-                }
+                // (b) sliced gathers into the (F+, k) pairs
+                gather_pass<PREC>(P, g, lane, (unsigned char*)Fk);
                 gs.sync();
             }
 
@@ -1091,6 +1184,25 @@ __device__ void run_group(const PlanDev& P, const OptsDev& O, const unsigned cha
                 gs.sync();
             }
 
+            // QSS (FP64 form): the predictor into nxt, then (a) and (b) of the
+            // predicted state at t + h into Fk2; the corrector in (d) then
+            // overwrites nxt.  (F+, k) of the current state stay in Fk, so a
+            // rejected attempt repeats only this part.
+            if (QSS) {
+                qss_predict(P, g, lane, cur, S.h);
+                if (lane == 0 && !S.constant) {
+                    const double sp = (S.t + S.h) * S.inv_tau;
+                    const double xm = P.cmax * sp;
+                    S.s_p = sp;
+                    S.poly_p = xm <= 1e-6 ? 2 : (xm <= 0.0009765625 ? 5 : 9);
+                }
+                gs.sync();
+                flux_pass<PREC>(P, g, lane, G, nxt, S.constant, S.s_p, 0.f, S.poly_p, false);
+                gs.sync();
+                gather_pass<PREC>(P, g, lane, (unsigned char*)g.Fk2);
+                gs.sync();
+            }
+
             // (d) update and error measures, then (e) the decision (lane 0)
             // while warps 1.. compute (a) for the candidate state at t + h,
             // as the next step needs it if this one is accepted
@@ -1100,7 +1212,7 @@ __device__ void run_group(const PlanDev& P, const OptsDev& O, const unsigned cha
                 S.u_spec = S.constant ? 0.f : __fmul_rn(__double2float_rn(S.t + h_now), S.u_scale);
                 S.refresh_spec = !P.rate_cache || !(fabsf(S.u_spec - S.u_ref) <= P.u_tol);
             }
-            update_reduce<PREC>(P, O, g, lane, cur, h_now, PREC == kPrecMixed ? S.h32 : (float)h_now, z);
+            update_reduce<PREC, QSS>(P, O, g, lane, cur, h_now, PREC == kPrecMixed ? S.h32 : (float)h_now, z);
             gs.sync();
             if (spec && lane >= 32)
                 flux_pass<PREC>(P, g, lane - 32, G - 32, nxt, S.constant, 0.0, S.u_spec, 0, S.refresh_spec != 0);
@@ -1225,7 +1337,7 @@ __device__ void run_group(const PlanDev& P, const OptsDev& O, const unsigned cha
 // ---------------------------------------------------------------------------
 // the persistent kernel
 // ---------------------------------------------------------------------------
-template <int PREC, bool FEAT>
+template <int PREC, bool FEAT, bool QSS>
 __global__ void __launch_bounds__(1024, 1) integrate_kernel(const __grid_constant__ LaunchParams lp) {
     extern __shared__ __align__(16) unsigned char smem[];
     __shared__ int s_go;
@@ -1273,7 +1385,7 @@ __global__ void __launch_bounds__(1024, 1) integrate_kernel(const __grid_constan
         const int g = threadIdx.x / P.G, lane = threadIdx.x - g * P.G;
         if (g < P.M) {
             GroupSync gs{1 + g, P.G, P.M == 1 && P.G == (int)blockDim.x};
-            run_group<PREC, FEAT>(P, lp.o, tb, smem, smem + toff + g * P.gl.bytes, lane, gs);
+            run_group<PREC, FEAT, QSS>(P, lp.o, tb, smem, smem + toff + g * P.gl.bytes, lane, gs);
         }
         __syncthreads();
     }
@@ -1282,30 +1394,35 @@ __global__ void __launch_bounds__(1024, 1) integrate_kernel(const __grid_constan
 cudaError_t launch_integrator(const LaunchParams& lp, int precision, int grid, int block,
                               cudaStream_t stream) {
     const bool feat = lp.o.learn || lp.o.record;
-    if (precision == kPrecFP64) {
+    if (precision == kPrecFP64 && lp.o.method) {
+        integrate_kernel<kPrecFP64, false, true><<<grid, block, lp.smem_bytes, stream>>>(lp);
+    } else if (precision == kPrecFP64) {
         if (feat)
-            integrate_kernel<kPrecFP64, true><<<grid, block, lp.smem_bytes, stream>>>(lp);
+            integrate_kernel<kPrecFP64, true, false><<<grid, block, lp.smem_bytes, stream>>>(lp);
         else
-            integrate_kernel<kPrecFP64, false><<<grid, block, lp.smem_bytes, stream>>>(lp);
+            integrate_kernel<kPrecFP64, false, false><<<grid, block, lp.smem_bytes, stream>>>(lp);
     } else if (precision == kPrecMixed64) {
         if (feat)
-            integrate_kernel<kPrecMixed64, true><<<grid, block, lp.smem_bytes, stream>>>(lp);
+            integrate_kernel<kPrecMixed64, true, false><<<grid, block, lp.smem_bytes, stream>>>(lp);
         else
-            integrate_kernel<kPrecMixed64, false><<<grid, block, lp.smem_bytes, stream>>>(lp);
+            integrate_kernel<kPrecMixed64, false, false><<<grid, block, lp.smem_bytes, stream>>>(lp);
     } else {
         if (feat)
-            integrate_kernel<kPrecMixed, true><<<grid, block, lp.smem_bytes, stream>>>(lp);
+            integrate_kernel<kPrecMixed, true, false><<<grid, block, lp.smem_bytes, stream>>>(lp);
         else
-            integrate_kernel<kPrecMixed, false><<<grid, block, lp.smem_bytes, stream>>>(lp);
+            integrate_kernel<kPrecMixed, false, false><<<grid, block, lp.smem_bytes, stream>>>(lp);
     }
     return cudaGetLastError();
 }
 
 cudaError_t integrator_set_smem_limit(int bytes) {
-    const void* fns[] = {(const void*)integrate_kernel<kPrecFP64, false>, (const void*)integrate_kernel<kPrecFP64, true>,
-                         (const void*)integrate_kernel<kPrecMixed, false>, (const void*)integrate_kernel<kPrecMixed, true>,
-                         (const void*)integrate_kernel<kPrecMixed64, false>,
-                         (const void*)integrate_kernel<kPrecMixed64, true>};
+    const void* fns[] = {(const void*)integrate_kernel<kPrecFP64, false, false>,
+                         (const void*)integrate_kernel<kPrecFP64, true, false>,
+                         (const void*)integrate_kernel<kPrecMixed, false, false>,
+                         (const void*)integrate_kernel<kPrecMixed, true, false>,
+                         (const void*)integrate_kernel<kPrecMixed64, false, false>,
+                         (const void*)integrate_kernel<kPrecMixed64, true, false>,
+                         (const void*)integrate_kernel<kPrecFP64, false, true>};
     for (const void* f : fns) {
         const cudaError_t e = cudaFuncSetAttribute(f, cudaFuncAttributeMaxDynamicSharedMemorySize, bytes);
         if (e != cudaSuccess) return e;
@@ -1317,12 +1434,12 @@ cudaError_t integrator_occupancy(int precision, int block, int smem, int* blocks
     // the FEAT variants use the same shared memory model; occupancy is governed
     // by shared memory and block size
     if (precision == kPrecFP64)
-        return cudaOccupancyMaxActiveBlocksPerMultiprocessor(blocks_per_sm, integrate_kernel<kPrecFP64, false>,
+        return cudaOccupancyMaxActiveBlocksPerMultiprocessor(blocks_per_sm, integrate_kernel<kPrecFP64, false, false>,
                                                              block, smem);
     if (precision == kPrecMixed64)
-        return cudaOccupancyMaxActiveBlocksPerMultiprocessor(blocks_per_sm, integrate_kernel<kPrecMixed64, false>,
+        return cudaOccupancyMaxActiveBlocksPerMultiprocessor(blocks_per_sm, integrate_kernel<kPrecMixed64, false, false>,
                                                              block, smem);
-    return cudaOccupancyMaxActiveBlocksPerMultiprocessor(blocks_per_sm, integrate_kernel<kPrecMixed, false>, block,
+    return cudaOccupancyMaxActiveBlocksPerMultiprocessor(blocks_per_sm, integrate_kernel<kPrecMixed, false, false>, block,
                                                          smem);
 }
 

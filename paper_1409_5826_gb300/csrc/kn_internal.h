@@ -71,6 +71,8 @@ struct GroupLayout {
                         //   high parts in the mixed form), entry N the constant 1
     int32_t off_Fk;     // real[N][2]: (F+_i, k_i) pairs
     int32_t off_carry;  // real[1]: the spare slot padding lanes of the gather store to
+    int32_t off_Fk2;    // real[N][2] + spare slot (QSS): (F+_i, k_i) of the predicted state, at the
+                        //   same distance from its spare slot as Fk (absent otherwise)
     int32_t off_red;    // per-warp reduction scratch, W = G/32 warps: double[W] x 3, float[W], int[W]
     int32_t off_feat;   // learned proposal / records: float[64 feats, 64 inputs, 128 h1, 128 h2],
                         //   int[3][64] histograms + 4 counters (absent when unused)
@@ -85,7 +87,8 @@ struct GroupState {
     long long steps, rejects;
     int zone, status, nrej, rhs_valid;
     int cur, done, valid, clipped;
-    int constant, poly, pad0, pad1;  // poly: 0 none (constant), 2/5 Taylor degree, 9 full exp
+    int constant, poly, poly_p, pad1;  // poly: 0 none (constant), 2/5 Taylor degree, 9 full exp;
+                                       //   poly_p: the same at t + h (QSS predicted state)
     float u;                         // s / ln 2 for the mixed rate factor
     float pad2[3];
     // learned proposal / records
@@ -106,6 +109,7 @@ struct GroupState {
     float dt32;     // the controller's next step
     float dtp32;    // the plain controller's proposal for the current state
     float pad3;
+    double s_p;     // QSS: (t + h) / tau, the profile time of the predicted state
 };
 
 struct PlanDev {
@@ -185,6 +189,7 @@ struct OptsDev {
     long long trace_cap;
     unsigned long long* trace_count;
     int follow_label;  // records: the attempt takes the label's step (perfect proposal)
+    int method;        // 0: Eq. (3) with the kappa switch; 1: alpha-QSS (FP64 form)
     long long* zone_ns;  // [zones][2]: global timer at queue fetch and at write-back (NULL: off)
     int learn;   // 1: propose with the network
     int record;  // 1: write (features, label) at every accepted state

@@ -22,6 +22,7 @@ KN_OK, KN_ERR_INVALID_ARG, KN_ERR_CUDA, KN_ERR_NOMEM, KN_ERR_STATE, KN_ERR_INTER
 ZONE_STATUS = {0: "ok", 1: "step_limit", 2: "dt_underflow", 3: "nonfinite", 4: "max_reject",
                5: "invalid", 6: "pending"}
 PREC_FP64, PREC_MIXED, PREC_MIXED_FP64 = 0, 1, 2
+METHOD_ASYMPTOTIC, METHOD_QSS = 0, 1
 MEM_HOST, MEM_DEVICE = 0, 1
 
 
@@ -53,7 +54,7 @@ class _Opts(C.Structure):
                 ("record_capacity", C.c_int64), ("record_count", C.c_void_p), ("mlp_margin", C.c_double),
                 ("trace_features", C.c_void_p), ("trace_out", C.c_void_p), ("trace_dt", C.c_void_p),
                 ("trace_capacity", C.c_int64), ("trace_count", C.c_void_p), ("follow_label", C.c_int32),
-                ("pad_", C.c_int32), ("zone_ns", C.c_void_p)]
+                ("method", C.c_int32), ("zone_ns", C.c_void_p)]
 
 
 class _Stats(C.Structure):
@@ -164,6 +165,7 @@ class Opts:
     trace_capacity: int = 0
     trace_count: int = 0
     follow_label: int = 0
+    method: int = METHOD_ASYMPTOTIC
     zone_ns: int = 0
 
     _PTRS = ("replay_dt", "replay_off", "replay_len", "mlp", "record_features", "record_labels", "record_count",

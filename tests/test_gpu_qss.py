@@ -1,0 +1,184 @@
+"""GPU parity of the alpha-QSS update (KN_METHOD_QSS, FP64 form) against the
+oracle's QSS (the alternative to Eq. 3 that Sec. 11 proposes).
+
+Tiers as for Eq. 3:
+  1. one step from identical states (kn_probe_step): F+ and k of the start
+     state, and Y' element by element;
+  2. the oracle's accepted dt sequence replayed: end states element by
+     element at 1e-9 (the FP64 bar);
+  3. free-running: the GPU's controller against the oracle's, step counts
+     within 2 % and end states within 10 eps_r.
+
+Tier-1 tolerance: 1e-12 on the scale max(Y, Y'), as for Eq. 3.  Both sides
+evaluate the update y + h (f - k y)/(1 + alpha k h) in the form without
+cancellation (c0 y + c1 h f)/c2; printed as a difference, the predictor of a
+species destroyed with k h >> 1 would keep a relative error of about
+eps (k h)^2 / 12, and rounding differences would reach Y' amplified (up to
+1e-6 on these inputs, against 4e-15 with the form used).
+"""
+import numpy as np
+import pytest
+
+from kn_inputs import (Zones, chain_network, constant_zones, net150, net365, profile_zones)
+
+pytestmark = pytest.mark.gpu
+
+FP64, MIXED, M64 = 0, 1, 2
+QSS = 1
+
+
+@pytest.fixture(scope="module")
+def kn():
+    import torch
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+    from paper_1409_5826_gb300 import build, kn as knmod
+    build.build()
+    return knmod
+
+
+def _rel_err(a, b, floor):
+    m = np.abs(b) > floor
+    if not m.any():
+        return 0.0
+    return float(np.max(np.abs(a[m] - b[m]) / np.abs(b[m])))
+
+
+def _random_states(net, Z, seed):
+    rng = np.random.default_rng(seed)
+    Y = 10.0 ** rng.uniform(-14, 0, (Z, net.n_species))
+    Y[rng.uniform(size=Y.shape) < 0.1] = 0.0
+    Y /= (Y * net.A).sum(1, keepdims=True)
+    return Y
+
+
+def _oracle_qss_step(orc, Y, k, kq, dt):
+    Fp0, k0, _ = orc.rhs(k, Y)
+    Yp = orc.qss_predict(Y, Fp0, k0, dt)
+    Fpp, kp, _ = orc.rhs(kq, Yp)
+    return orc.qss_correct(Y, Fp0, k0, Fpp, kp, dt), Fp0, k0
+
+
+@pytest.mark.parametrize("factory", [chain_network, net150, net365])
+@pytest.mark.parametrize("tiling", [(0, 0), (32, 32), (128, 256)])
+def test_qss_one_step_parity(kn, oracle_mod, factory, tiling):
+    net = factory()
+    orc = oracle_mod.Oracle(net)
+    Z = 37
+    Y = _random_states(net, Z, 5)
+    rng = np.random.default_rng(1)
+    T0 = rng.uniform(2, 7, Z)
+    rho0 = 10 ** rng.uniform(7, 9, Z)
+    tau = np.where(np.arange(Z) % 3 == 0, 0.0, 10 ** rng.uniform(-1, 0, Z))
+    ts = 10 ** rng.uniform(-12, -9, Z)
+    dt = 10 ** rng.uniform(-16, -9, Z)
+    z = Zones(Y0=Y, T0=T0, rho0=rho0, tau=tau, t_start=ts, t_end=np.ones(Z), dt_trial=dt)
+    g = kn.Network(net)
+    g.set_zones(z)
+    G, P = tiling
+    if net.n_species == 365 and P > G:
+        with pytest.raises(kn.KnError, match="no tiling fits"):
+            g.probe(kn.Opts(precision=FP64, method=QSS, threads_per_zone=G, threads_per_cta=P))
+        return
+    out = g.probe(kn.Opts(precision=FP64, method=QSS, threads_per_zone=G, threads_per_cta=P))
+    for i in range(Z):
+        T9, rho = orc.conditions(T0[i], rho0[i], tau[i], ts[i])
+        T9p, rhop = orc.conditions(T0[i], rho0[i], tau[i], ts[i] + dt[i])
+        k, kq = orc.rates(T9, rho), orc.rates(T9p, rhop)
+        Yc, Fp0, k0 = _oracle_qss_step(orc, Y[i], k, kq, dt[i])
+        assert _rel_err(out["Fp"][i], Fp0, 1e-300) < 1e-12, ("F+", i)
+        assert _rel_err(out["k"][i], k0, 1e-300) < 1e-12, ("k", i)
+        scale = np.maximum(Y[i], Yc)
+        m = scale > 1e-30
+        err = float(np.max(np.abs(out["Y1"][i][m] - Yc[m]) / scale[m]))
+        assert err < 1e-12, ("Y1", i, err)
+
+
+def _replay(kn, net, zones, dts_list):
+    import torch
+    g = kn.Network(net)
+    g.set_zones(zones)
+    lens = np.array([len(d) for d in dts_list], np.int64)
+    off = np.concatenate([[0], np.cumsum(lens)[:-1]]).astype(np.int64)
+    flat = np.concatenate(dts_list) if lens.sum() else np.zeros(1)
+    dev = torch.device("cuda")
+    t_dt = torch.from_numpy(flat).to(dev)
+    t_off = torch.from_numpy(off).to(dev)
+    t_len = torch.from_numpy(lens).to(dev)
+    o = kn.Opts(precision=FP64, method=QSS, replay_dt=t_dt.data_ptr(), replay_off=t_off.data_ptr(),
+                replay_len=t_len.data_ptr())
+    kn.integrate_batch([g], o)
+    r = g.get()
+    del t_dt, t_off, t_len
+    return r
+
+
+@pytest.mark.parametrize("case", ["chain_constant", "chain_profiles", "net150_profiles"])
+def test_qss_replay_parity(kn, oracle_mod, case):
+    if case == "chain_constant":
+        net = chain_network()
+        z = constant_zones(net)
+    elif case == "chain_profiles":
+        net = chain_network()
+        z = profile_zones(net, 6, t_end=1e-3)
+    else:
+        net = net150()
+        z = profile_zones(net, 6, t_end=1e-10)
+    orc = oracle_mod.Oracle(net)
+    opts = oracle_mod.OracleOpts(method=QSS)
+    rec = [orc.integrate(z, i, opts, record=10 ** 6) for i in range(z.n_zones)]
+    r = _replay(kn, net, z, [x["dts"] for x in rec])
+    for i in range(z.n_zones):
+        assert r["status"][i] == 0 and r["steps"][i] == rec[i]["steps"]
+        assert r["t"][i] == rec[i]["t"]
+        err = _rel_err(r["Y"][i], rec[i]["Y"], 1e-10)
+        assert err < 1e-9, (i, err)
+
+
+@pytest.mark.parametrize("case", ["chain_profiles", "net150_profiles"])
+def test_qss_free_running(kn, oracle_mod, case):
+    if case == "chain_profiles":
+        net = chain_network()
+        z = profile_zones(net, 12, t_end=1e-2)
+    else:
+        net = net150()
+        z = profile_zones(net, 8, t_end=1e-10)
+    orc = oracle_mod.Oracle(net)
+    opts = oracle_mod.OracleOpts(method=QSS)
+    g = kn.Network(net)
+    g.set_zones(z)
+    kn.integrate_batch([g], kn.Opts(precision=FP64, method=QSS))
+    r = g.get()
+    for i in range(z.n_zones):
+        o = orc.integrate(z, i, opts)
+        assert r["status"][i] == 0 and o["status"] == 0
+        assert r["t"][i] == o["t"]
+        assert abs(r["steps"][i] - o["steps"]) <= 0.02 * o["steps"] + 2, (i, r["steps"][i], o["steps"])
+        assert _rel_err(r["Y"][i], o["Y"], 1e-10) < 10 * 0.05, i
+
+
+def test_qss_differs_from_asymptotic_and_is_deterministic(kn):
+    """The method switch reaches the kernel: QSS and Eq. 3 take different step
+    counts on the chain, and two QSS runs agree bit for bit."""
+    net = chain_network()
+    z = profile_zones(net, 8, t_end=1e-3)
+    res = []
+    for method in (0, QSS, QSS):
+        g = kn.Network(net)
+        g.set_zones(z)
+        kn.integrate_batch([g], kn.Opts(precision=FP64, method=method))
+        res.append(g.get())
+    assert not np.array_equal(res[0]["steps"], res[1]["steps"])
+    assert np.array_equal(res[1]["steps"], res[2]["steps"])
+    assert np.array_equal(res[1]["Y"], res[2]["Y"])
+
+
+def test_qss_refuses_other_forms(kn):
+    net = chain_network()
+    g = kn.Network(net)
+    g.set_zones(constant_zones(net))
+    for prec in (MIXED, M64):
+        with pytest.raises(kn.KnError, match="KN_METHOD_QSS"):
+            kn.integrate_batch([g], kn.Opts(precision=prec, method=QSS))
+    with pytest.raises(kn.KnError, match="opts.method"):
+        kn.integrate_batch([g], kn.Opts(precision=FP64, method=7))
