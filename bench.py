@@ -568,6 +568,7 @@ def other_forms(kn, g, net, zones, dz, stream, flush, mixed_line, args):
     out["perfect_proposal_ceiling"] = perfect_proposal(kn, g, dz, stream)
     # the uneven-size batch: 16/48 : 150/1604 : 365/4400 = 1:2:1 in one launch
     out["uneven_sizes"] = uneven_sizes(kn, stream, flush, n_sms, args)
+    out["qss_chain"] = qss_chain(kn, stream, flush, fp64_peak)
     out["note"] = ("every form: warm-up batches, then timed batches with CUDA events on the launching stream, "
                    "L2 flushed between batches, clocks sampled; errors against an oracle run at eps_r 0.005, "
                    "eps_c 1e-7 on 8 zones of the batch")
@@ -637,6 +638,47 @@ def perfect_proposal(kn, g, dz, stream):
                    "that fails), clipped to [dt_plain, 16 dt_plain]; attempts_ratio is the most a learned "
                    "proposal could save")
     return res
+
+
+def qss_chain(kn, stream, flush, fp64_peak):
+    """The alpha-QSS update against Eq. 3, both in FP64, on 4096 zones of the
+    16-species chain with profiles over 1e-12 -> 1e-2 s (where the oracle
+    takes 3-4x fewer steps with QSS), each with its roofline and its
+    end-state error against a 10x-tighter Eq. 3 oracle run on 8 zones."""
+    import torch
+    import oracle
+    from kn_inputs import chain_network, profile_zones
+    net = chain_network()
+    zones = profile_zones(net, 4096, base_seed=700_000, t_end=1e-2)
+    dev = torch.device("cuda", torch.cuda.current_device())
+    names = ("Y0", "T0", "rho0", "tau", "t_start", "t_end", "dt_trial")
+    dz = {k: torch.from_numpy(np.ascontiguousarray(getattr(zones, k))).to(dev) for k in names}
+    g = kn.Network(net)
+    pick = np.linspace(0, zones.n_zones - 1, 8).astype(int)
+    tight = oracle.Oracle(net).integrate_batch(zones.subset(pick), oracle.OracleOpts(eps_r=0.005, eps_c=1e-7),
+                                               threads=os.cpu_count() or 1)
+
+    def set_main():
+        g.set_zones(dz, stream)
+
+    out = {"workload": "4096 zones x 16sp/48rx chain, T9/rho profiles, t 1e-12 -> 1e-2 s"}
+    for name, method, count in (("asymptotic_fp64", kn.METHOD_ASYMPTOTIC, algorithmic_flops),
+                                ("qss_fp64", kn.METHOD_QSS, algorithmic_flops_qss)):
+        o = dict(precision=kn.PREC_FP64, method=method)
+        set_main()
+        tuned = kn.autotune([g], kn.Opts(**o), max_steps=3000, stream=stream)
+        tb = timed_batches(kn, [g], set_main, kn.Opts(**o, use_graph=1), 3, 3, stream, flush)
+        st = tb["stats"]
+        kms = _mean(tb["kernel_ms"])
+        roof = fp64_roofline(count(net, st["steps"], st["rejects"]), kms, fp64_peak,
+                             "as the 150-species forms' FP64 counts")
+        Y = g.get(stream)["Y"]
+        e = [np.median(np.abs(Y[i][m] - tight["Y"][a][m]) / tight["Y"][a][m])
+             for a, i in enumerate(pick) for m in [tight["Y"][a] > 1e-10]]
+        out[name] = _form_line(tb, [g], zones.n_zones, roof, {"median_rel_err_vs_tight_oracle": float(np.median(e)),
+                                                              "tiling": tuned})
+    out["qss_vs_asymptotic_zones_per_s"] = out["qss_fp64"]["zones_per_s"] / out["asymptotic_fp64"]["zones_per_s"]
+    return out
 
 
 def uneven_sizes(kn, stream, flush, n_sms, args):
