@@ -46,7 +46,7 @@ def _args():
     ap.add_argument("--steps", type=int, default=5)
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
-    ap.add_argument("--form", default="mixed", choices=["mixed", "mixed_fp64", "fp64", "qss_fp64"])
+    ap.add_argument("--form", default="mixed", choices=["mixed", "mixed_fp64", "fp64", "qss_fp64", "qss_mixed"])
     ap.add_argument("--zones", type=int, default=N_ZONES)
     ap.add_argument("--t-end", type=float, default=T_END, help="integration end time (s)")
     ap.add_argument("--strong", action="store_true",
@@ -401,14 +401,19 @@ def _mean(x):
     return float(np.mean(x))
 
 
-def smem_roofline(parts, kms, clk, n_sms):
+def smem_roofline(parts, kms, clk, n_sms, qss=False):
     """Shared-memory roofline of the FP32-flux forms: the measurement plan's
     bytes per accepted zone-step (algorithmic_smem_bytes, FP32 widths) over
     the kernel time, against 128 B/clk/SM x SMs x the sampled SM clock.
-    parts: [(network, accepted steps, rejects)]."""
+    parts: [(network, accepted steps, rejects)].  qss: the QSS update, whose
+    every attempt also runs the flux pass and the gathers of the predicted
+    state (the same bytes again per attempt)."""
     peak = 128.0 * n_sms * _sm_clock_hz(clk) / 1e9
-    b = sum(algorithmic_smem_bytes(n, st) for n, st, rj in parts)
-    bf = sum(full_smem_bytes(n, st, rj) for n, st, rj in parts)
+    b = sum(algorithmic_smem_bytes(n, st) + (algorithmic_smem_bytes(n, st + rj) if qss else 0.0)
+            for n, st, rj in parts)
+    bf = sum(full_smem_bytes(n, st, rj) + (full_smem_bytes(n, st + rj, 0) - 28 * n.n_species * (st + rj)
+                                          if qss else 0.0)
+             for n, st, rj in parts)
     return {"bound": "alu", "resource": "shared-memory bandwidth (SM-local)", "unit": "GB/s",
             "kernel": "integrate_kernel", "achieved": b / (kms / 1e3) / 1e9, "peak": peak,
             "frac": b / (kms / 1e3) / 1e9 / peak,
@@ -519,6 +524,17 @@ def other_forms(kn, g, net, zones, dz, stream, flush, mixed_line, args):
     out["qss_fp64"] = _form_line(tb, [g], zones.n_zones, roof, {"median_rel_err_vs_tight_oracle": err(),
                                                                 "tiling": tuned, "tail": tail_of(tb, tuned)})
     out["qss_vs_asymptotic_fp64_zones_per_s"] = out["qss_fp64"]["zones_per_s"] / out["fp64"]["zones_per_s"]
+    # the same in the mixed form, against the headline
+    g.set_zones(dz, stream)
+    qo = dict(precision=kn.PREC_MIXED, method=kn.METHOD_QSS)
+    tuned = kn.autotune([g], kn.Opts(**qo), max_steps=300, stream=stream)
+    tb = timed_batches(kn, [g], set_main, kn.Opts(**qo, use_graph=1), 3, 3, stream, flush, zns)
+    st = tb["stats"]
+    roof = smem_roofline([(net, st["steps"], st["rejects"])], _mean(tb["kernel_ms"]), tb["clocks"], n_sms,
+                         qss=True)
+    out["qss_mixed"] = _form_line(tb, [g], zones.n_zones, roof, {"median_rel_err_vs_tight_oracle": err(),
+                                                                 "tiling": tuned, "tail": tail_of(tb, tuned)})
+    out["qss_vs_asymptotic_mixed_zones_per_s"] = out["qss_mixed"]["zones_per_s"] / mixed_line["zones_per_s"]
     # the learned proposal: records from training zones, training on the GPU,
     # then the batch with the network proposing and the plain test judging
     t0 = time.perf_counter()
@@ -641,10 +657,11 @@ def perfect_proposal(kn, g, dz, stream):
 
 
 def qss_chain(kn, stream, flush, fp64_peak):
-    """The alpha-QSS update against Eq. 3, both in FP64, on 4096 zones of the
-    16-species chain with profiles over 1e-12 -> 1e-2 s (where the oracle
-    takes 3-4x fewer steps with QSS), each with its roofline and its
-    end-state error against a 10x-tighter Eq. 3 oracle run on 8 zones."""
+    """The alpha-QSS update against Eq. 3, in FP64 and in the mixed form, on
+    4096 zones of the 16-species chain with profiles over 1e-12 -> 1e-2 s
+    (where the oracle takes 3-4x fewer steps with QSS), each with its
+    roofline and its end-state error against a 10x-tighter Eq. 3 oracle run
+    on 8 zones."""
     import torch
     import oracle
     from kn_inputs import chain_network, profile_zones
@@ -662,22 +679,31 @@ def qss_chain(kn, stream, flush, fp64_peak):
         g.set_zones(dz, stream)
 
     out = {"workload": "4096 zones x 16sp/48rx chain, T9/rho profiles, t 1e-12 -> 1e-2 s"}
-    for name, method, count in (("asymptotic_fp64", kn.METHOD_ASYMPTOTIC, algorithmic_flops),
-                                ("qss_fp64", kn.METHOD_QSS, algorithmic_flops_qss)):
-        o = dict(precision=kn.PREC_FP64, method=method)
+    n_sms = _n_sms()
+    for name, prec, method, count in (("asymptotic_fp64", kn.PREC_FP64, kn.METHOD_ASYMPTOTIC, algorithmic_flops),
+                                      ("qss_fp64", kn.PREC_FP64, kn.METHOD_QSS, algorithmic_flops_qss),
+                                      ("asymptotic_mixed", kn.PREC_MIXED, kn.METHOD_ASYMPTOTIC, None),
+                                      ("qss_mixed", kn.PREC_MIXED, kn.METHOD_QSS, None)):
+        o = dict(precision=prec, method=method)
         set_main()
         tuned = kn.autotune([g], kn.Opts(**o), max_steps=3000, stream=stream)
         tb = timed_batches(kn, [g], set_main, kn.Opts(**o, use_graph=1), 3, 3, stream, flush)
         st = tb["stats"]
         kms = _mean(tb["kernel_ms"])
-        roof = fp64_roofline(count(net, st["steps"], st["rejects"]), kms, fp64_peak,
-                             "as the 150-species forms' FP64 counts")
+        if count:
+            roof = fp64_roofline(count(net, st["steps"], st["rejects"]), kms, fp64_peak,
+                                 "as the 150-species forms' FP64 counts")
+        else:
+            roof = smem_roofline([(net, st["steps"], st["rejects"])], kms, tb["clocks"], n_sms,
+                                 qss=method == kn.METHOD_QSS)
         Y = g.get(stream)["Y"]
         e = [np.median(np.abs(Y[i][m] - tight["Y"][a][m]) / tight["Y"][a][m])
              for a, i in enumerate(pick) for m in [tight["Y"][a] > 1e-10]]
         out[name] = _form_line(tb, [g], zones.n_zones, roof, {"median_rel_err_vs_tight_oracle": float(np.median(e)),
                                                               "tiling": tuned})
-    out["qss_vs_asymptotic_zones_per_s"] = out["qss_fp64"]["zones_per_s"] / out["asymptotic_fp64"]["zones_per_s"]
+    out["qss_vs_asymptotic_fp64_zones_per_s"] = out["qss_fp64"]["zones_per_s"] / out["asymptotic_fp64"]["zones_per_s"]
+    out["qss_vs_asymptotic_mixed_zones_per_s"] = (out["qss_mixed"]["zones_per_s"] /
+                                                  out["asymptotic_mixed"]["zones_per_s"])
     return out
 
 
@@ -779,8 +805,8 @@ def main():
     dz = {k: torch.from_numpy(np.ascontiguousarray(getattr(zones, k))).to(dev) for k in names}
     g = kn.Network(net)
     prec = {"mixed": kn.PREC_MIXED, "mixed_fp64": kn.PREC_MIXED_FP64, "fp64": kn.PREC_FP64,
-            "qss_fp64": kn.PREC_FP64}[args.form]
-    method = kn.METHOD_QSS if args.form == "qss_fp64" else kn.METHOD_ASYMPTOTIC
+            "qss_fp64": kn.PREC_FP64, "qss_mixed": kn.PREC_MIXED}[args.form]
+    method = kn.METHOD_QSS if args.form.startswith("qss") else kn.METHOD_ASYMPTOTIC
     stream = torch.cuda.current_stream()
     tuned = None
     if not (args.tpz or args.tpc):
@@ -853,7 +879,7 @@ def main():
     else:
         # SM-local bound: shared-memory bandwidth, 32 banks x 4 B per clock per
         # SM at the SM clock sampled during the timed steps
-        roof = smem_roofline([(net, st["steps"], st["rejects"])], kms, clk, n_sms)
+        roof = smem_roofline([(net, st["steps"], st["rejects"])], kms, clk, n_sms, qss=args.form == "qss_mixed")
     # DRAM traffic of the integrator from the committed ncu capture of this
     # kernel (small case, mixed form), scaled to this launch by zone count
     # (each zone's state is read once per launch); null when the kernel's
@@ -877,7 +903,7 @@ def main():
     elif args.tpz and args.tpc:
         groups = n_sms * (args.tpc // args.tpz)
     dtype = {"mixed": "f32 (float-float state)", "mixed_fp64": "f32 fluxes, f64 update", "fp64": "f64",
-             "qss_fp64": "f64"}[args.form]
+             "qss_fp64": "f64", "qss_mixed": "f32 (float-float state)"}[args.form]
     line = {"metric": METRIC, "value": value, "unit": "zone-steps/s", "n_gpus": world, "steps": args.steps,
             "warmup": max(3, args.warmup), "ms_per_step": ms / args.steps, "higher_is_better": True,
             "scaling": "strong" if args.strong else "weak", "vs_baseline": None, "dtype": dtype,

@@ -214,8 +214,12 @@ typedef struct {
        and the same accept test and step control.  Each update
        y + h (f - k y) / (1 + alpha k h) is evaluated in an algebraically equal
        form without its cancellation at k h >> 1, which is non-negative for
-       non-negative inputs.  Each attempt evaluates the right-hand side twice.  Only with KN_PREC_FP64, and not combined with
-       mlp, record_features or follow_label (KN_ERR_INVALID_ARG otherwise). */
+       non-negative inputs.  Each attempt evaluates the right-hand side twice.
+       With KN_PREC_FP64 every step is FP64; with KN_PREC_MIXED the predictor
+       and the predicted state's fluxes and gathers are FP32 and the corrector
+       updates the float-float pairs as Eq. (3) does (the change added up to
+       k dt = 1, y' itself above).  Not with KN_PREC_MIXED_FP64, mlp,
+       record_features or follow_label (KN_ERR_INVALID_ARG). */
     int32_t method;
     /* Per-zone timing (measurement): zone_ns [total zones][2] (device int64)
        receives the GPU global timer, in ns, when a zone group takes the zone

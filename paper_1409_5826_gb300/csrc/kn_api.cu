@@ -387,8 +387,10 @@ static kn_status validate_opts(const kn_opts* o) {
         return fail(KN_ERR_INVALID_ARG, "opts.follow_label needs opts.record_features");
     if (o->method != KN_METHOD_ASYMPTOTIC && o->method != KN_METHOD_QSS)
         return fail(KN_ERR_INVALID_ARG, "opts.method must be KN_METHOD_ASYMPTOTIC or KN_METHOD_QSS");
-    if (o->method == KN_METHOD_QSS && (o->precision != KN_PREC_FP64 || o->mlp || o->record_features))
-        return fail(KN_ERR_INVALID_ARG, "opts.method KN_METHOD_QSS runs in KN_PREC_FP64 without mlp or records");
+    if (o->method == KN_METHOD_QSS &&
+        (o->precision == KN_PREC_MIXED_FP64 || o->mlp || o->record_features))
+        return fail(KN_ERR_INVALID_ARG,
+                    "opts.method KN_METHOD_QSS runs in KN_PREC_FP64 or KN_PREC_MIXED, without mlp or records");
     if ((o->replay_dt != nullptr) != (o->replay_off != nullptr) ||
         (o->replay_dt != nullptr) != (o->replay_len != nullptr))
         return fail(KN_ERR_INVALID_ARG, "opts.replay_dt/off/len must be set together");

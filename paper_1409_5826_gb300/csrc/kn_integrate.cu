@@ -163,7 +163,7 @@ struct GroupPtrs {
 // ---------------------------------------------------------------------------
 // The explicit quasi-steady-state update (Sec. 11 proposes it as the
 // alternative to Eq. 3; its formula is the alpha-QSS predictor-corrector of
-// Mott, Oran & van Leer, J. Comput. Phys. 164 (2000) 407).  FP64 form only.
+// Mott, Oran & van Leer, J. Comput. Phys. 164 (2000) 407).  FP64 and mixed forms.
 // ---------------------------------------------------------------------------
 
 // alpha(x), x = k dt >= 0, is the rational approximation
@@ -226,6 +226,57 @@ __device__ __forceinline__ void qss_predict(const PlanDev& P, const GroupPtrs& g
     const double* Yc = g.Y64 + cur * NP1;
     double* Yp = g.Y64 + (cur ^ 1) * NP1;
     for (int i = lane; i < N; i += G) Yp[i] = qss_update1(Yc[i], Fk[2 * i], Fk[2 * i + 1], h);
+}
+
+// FP32 versions for the mixed form.  In powers of r = 1/x above x = 1 the
+// c1 h f term is written (c1 / r) (f / k), since h r = 1/k: nothing then
+// overflows or underflows before the result does (x up to FLT_MAX).  The
+// denominators d and c2 lie in [1, 685], so the approximate division
+// __fdividef (2 ulp) is exact enough; f / k and 1/x use the correctly rounded
+// division and reciprocal.
+__device__ __forceinline__ void qss_weights32(float x, float& a, float& b) {
+    float n, d, dn;
+    if (x <= 1.f) {
+        n = fmaf(fmaf(x + 11.f, x, 60.f), x, 180.f);
+        d = fmaf(fmaf(x + 12.f, x, 60.f), x, 360.f);
+        dn = fmaf(x, x, 180.f);
+    } else {
+        const float r = __frcp_rn(x);
+        n = fmaf(fmaf(fmaf(180.f, r, 60.f), r, 11.f), r, 1.f);
+        d = fmaf(fmaf(fmaf(360.f, r, 60.f), r, 12.f), r, 1.f);
+        dn = r * fmaf(180.f * r, r, 1.f);
+    }
+    a = __fdividef(n, d);
+    b = __fdividef(dn, d);
+}
+
+__device__ __forceinline__ float qss_update1_32(float y, float f, float k, float h) {
+    const float x = __fmul_rn(k, h);
+    if (x <= 1.f) {
+        const float c0 = fmaf(fmaf(12.f, x, -120.f), x, 360.f);
+        const float c1 = fmaf(fmaf(x + 12.f, x, 60.f), x, 360.f);
+        const float c2 = fmaf(fmaf(fmaf(x + 12.f, x, 72.f), x, 240.f), x, 360.f);
+        return __fdividef(fmaf(c0, y, c1 * __fmul_rn(h, f)), c2);
+    }
+    const float r = __frcp_rn(x);
+    const float c0 = fmaf(fmaf(360.f, r, -120.f), r, 12.f) * __fmul_rn(r, r);
+    const float c1r = fmaf(fmaf(fmaf(360.f, r, 60.f), r, 12.f), r, 1.f);  // c1 / r
+    const float c2 = fmaf(fmaf(fmaf(fmaf(360.f, r, 240.f), r, 72.f), r, 12.f), r, 1.f);
+    return __fdividef(fmaf(c0, y, c1r * __fdiv_rn(f, k)), c2);
+}
+
+// Mixed form predictor: the FP32 copy of Yp (all the predicted state's flux
+// pass reads) into buffer nxt, from the high parts of the current pairs.
+__device__ __forceinline__ void qss_predict_mixed(const PlanDev& P, const GroupPtrs& g, int lane, int cur,
+                                                  float h32) {
+    const int N = P.N, G = P.G, NP1 = N + 1;
+    const float2* Fk = (const float2*)g.Fk;
+    const float* Yh = g.Y32 + cur * NP1;
+    float* Yp = g.Y32 + (cur ^ 1) * NP1;
+    for (int i = lane; i < N; i += G) {
+        const float2 fk = Fk[i];
+        Yp[i] = qss_update1_32(Yh[i], fk.x, fk.y, h32);
+    }
 }
 
 // (d) the update with step h from buffer cur into nxt, and each warp's share
@@ -310,10 +361,16 @@ __device__ __forceinline__ void two_sum(float a, float b, float& s, float& e) {
 // pair exactly up to one rounding of the low part.  The conservation sum
 // sum A (y' - y) is a float-float sum of exact products, so it resolves the
 // stored change far below eps_c; no FP64 instruction runs per species.
+// QSS: the alpha-QSS corrector in place of Eq. 3 (F+p, kp of the predicted
+// state in Fk2).  Up to k h = 1 its change h (f~ - kbar y)/(1 + a k h) is added
+// to the pair as on Eq. 3's explicit branch; above, y' itself is computed in
+// the form without cancellation, as on Eq. 3's asymptotic branch.
+template <bool QSS>
 __device__ __forceinline__ void update_reduce_mixed(const PlanDev& P, const OptsDev& O, const GroupPtrs& g, int lane,
                                                     int cur, float h32, int z) {
     const int N = P.N, G = P.G, NP1 = N + 1;
-    const float2* Fk = (const float2*)g.Fk;  // (F+_i, k_i)
+    const float2* Fk = (const float2*)g.Fk;
+    const float2* Fk2 = (const float2*)g.Fk2;  // (F+_i, k_i)
     const float* A = (const float*)g.A;
     const float* Yh = g.Y32 + cur * NP1;
     const float* Yl = g.Ylo + cur * NP1;
@@ -327,7 +384,26 @@ __device__ __forceinline__ void update_reduce_mixed(const PlanDev& P, const Opts
         const float yh = Yh[i], yl = Yl[i], fp = fk.x, kk = fk.y;
         const float kdt = __fmul_rn(kk, h32);
         float nh, nl, dh, dl;
-        if (kdt >= O.kappa32) {
+        if (QSS) {
+            const float2 fkp = Fk2[i];
+            const float kbar = 0.5f * (kk + fkp.y);
+            const float x = __fmul_rn(kbar, h32);
+            float a, b;
+            qss_weights32(x, a, b);
+            const float ft = fmaf(a, fkp.x, b * fp);
+            if (x <= 1.f) {
+                dh = __fdividef(__fmul_rn(h32, fmaf(-kbar, yh, ft)), fmaf(a, x, 1.f));
+                dl = 0.f;
+                float s, e;
+                two_sum(yh, dh, s, e);
+                two_sum(s, __fadd_rn(e, yl), nh, nl);
+            } else {
+                nh = qss_update1_32(yh, ft, kbar, h32);
+                nl = 0.f;
+                two_sum(nh, -yh, dh, dl);
+                dl = __fsub_rn(dl, yl);
+            }
+        } else if (kdt >= O.kappa32) {
             // 1 + k dt >= 2; __fdividef is within 2 ulp below 2^126 and gives
             // 0 above it (an abundance below 2^-126 of y + dt F+)
             nh = __fdividef(fmaf(h32, fp, yh), __fadd_rn(1.f, kdt));
@@ -482,7 +558,7 @@ template <int PREC, bool QSS = false>
 __device__ __forceinline__ void update_reduce(const PlanDev& P, const OptsDev& O, const GroupPtrs& g, int lane,
                                               int cur, double h, float h32, int z) {
     if (PREC == kPrecMixed)
-        update_reduce_mixed(P, O, g, lane, cur, h32, z);
+        update_reduce_mixed<QSS>(P, O, g, lane, cur, h32, z);
     else if (PREC == kPrecMixed64)
         update_reduce_mixed64(P, O, g, lane, cur, h, z);
     else
@@ -1027,6 +1103,8 @@ __device__ void run_group(const PlanDev& P, const OptsDev& O, const unsigned cha
                 S.poly = 0;
                 S.s_p = 0.0;
                 S.poly_p = 0;
+                S.u_p = 0.f;
+                S.refresh_p = 0;
                 S.u = 0.f;
                 S.u_ref = -1e30f;  // the first flux pass computes the cached rates
                 S.steps = 0;
@@ -1184,21 +1262,35 @@ __device__ void run_group(const PlanDev& P, const OptsDev& O, const unsigned cha
                 gs.sync();
             }
 
-            // QSS (FP64 form): the predictor into nxt, then (a) and (b) of the
-            // predicted state at t + h into Fk2; the corrector in (d) then
-            // overwrites nxt.  (F+, k) of the current state stay in Fk, so a
-            // rejected attempt repeats only this part.
+            // QSS: the predictor into nxt, then (a) and (b) of the predicted
+            // state at t + h into Fk2; the corrector in (d) then overwrites
+            // nxt.  (F+, k) of the current state stay in Fk, so a rejected
+            // attempt repeats only this part.  FP32-flux form: the predictor
+            // writes the FP32 copy the flux pass reads, and the predicted
+            // pass refreshes the cached rates at (t + h) when they are stale
+            // (each thread the reactions it reads, as in the main pass).
             if (QSS) {
-                qss_predict(P, g, lane, cur, S.h);
+                if (PREC == kPrecFP64)
+                    qss_predict(P, g, lane, cur, S.h);
+                else
+                    qss_predict_mixed(P, g, lane, cur, S.h32);
                 if (lane == 0 && !S.constant) {
-                    const double sp = (S.t + S.h) * S.inv_tau;
-                    const double xm = P.cmax * sp;
-                    S.s_p = sp;
-                    S.poly_p = xm <= 1e-6 ? 2 : (xm <= 0.0009765625 ? 5 : 9);
+                    if (PREC == kPrecFP64) {
+                        const double sp = (S.t + S.h) * S.inv_tau;
+                        const double xm = P.cmax * sp;
+                        S.s_p = sp;
+                        S.poly_p = xm <= 1e-6 ? 2 : (xm <= 0.0009765625 ? 5 : 9);
+                    } else {
+                        S.u_p = __fmul_rn(__double2float_rn(S.t + (double)S.h32), S.u_scale);
+                    }
                 }
+                if (lane == 0 && PREC != kPrecFP64)
+                    S.refresh_p = !P.rate_cache || !(fabsf(S.u_p - S.u_ref) <= P.u_tol);
                 gs.sync();
-                flux_pass<PREC>(P, g, lane, G, nxt, S.constant, S.s_p, 0.f, S.poly_p, false);
+                flux_pass<PREC>(P, g, lane, G, nxt, S.constant, S.s_p, S.u_p, S.poly_p,
+                                PREC != kPrecFP64 && S.refresh_p != 0);
                 gs.sync();
+                if (lane == 0 && PREC != kPrecFP64 && S.refresh_p) S.u_ref = S.u_p;
                 gather_pass<PREC>(P, g, lane, (unsigned char*)g.Fk2);
                 gs.sync();
             }
@@ -1396,6 +1488,8 @@ cudaError_t launch_integrator(const LaunchParams& lp, int precision, int grid, i
     const bool feat = lp.o.learn || lp.o.record;
     if (precision == kPrecFP64 && lp.o.method) {
         integrate_kernel<kPrecFP64, false, true><<<grid, block, lp.smem_bytes, stream>>>(lp);
+    } else if (precision == kPrecMixed && lp.o.method) {
+        integrate_kernel<kPrecMixed, false, true><<<grid, block, lp.smem_bytes, stream>>>(lp);
     } else if (precision == kPrecFP64) {
         if (feat)
             integrate_kernel<kPrecFP64, true, false><<<grid, block, lp.smem_bytes, stream>>>(lp);
@@ -1422,7 +1516,8 @@ cudaError_t integrator_set_smem_limit(int bytes) {
                          (const void*)integrate_kernel<kPrecMixed, true, false>,
                          (const void*)integrate_kernel<kPrecMixed64, false, false>,
                          (const void*)integrate_kernel<kPrecMixed64, true, false>,
-                         (const void*)integrate_kernel<kPrecFP64, false, true>};
+                         (const void*)integrate_kernel<kPrecFP64, false, true>,
+                         (const void*)integrate_kernel<kPrecMixed, false, true>};
     for (const void* f : fns) {
         const cudaError_t e = cudaFuncSetAttribute(f, cudaFuncAttributeMaxDynamicSharedMemorySize, bytes);
         if (e != cudaSuccess) return e;

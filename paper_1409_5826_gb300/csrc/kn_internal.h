@@ -87,8 +87,9 @@ struct GroupState {
     long long steps, rejects;
     int zone, status, nrej, rhs_valid;
     int cur, done, valid, clipped;
-    int constant, poly, poly_p, pad1;  // poly: 0 none (constant), 2/5 Taylor degree, 9 full exp;
-                                       //   poly_p: the same at t + h (QSS predicted state)
+    int constant, poly, poly_p, refresh_p;  // poly: 0 none (constant), 2/5 Taylor degree, 9 full exp;
+                                            //   poly_p: the same at t + h (QSS predicted state);
+                                            //   refresh_p: the QSS predicted pass recomputes Kc
     float u;                         // s / ln 2 for the mixed rate factor
     float pad2[3];
     // learned proposal / records
@@ -108,7 +109,7 @@ struct GroupState {
     float h32;      // the current attempt's step
     float dt32;     // the controller's next step
     float dtp32;    // the plain controller's proposal for the current state
-    float pad3;
+    float u_p;      // QSS, FP32-flux forms: (t + h)/(tau ln 2) of the predicted state
     double s_p;     // QSS: (t + h) / tau, the profile time of the predicted state
 };
 
@@ -189,7 +190,7 @@ struct OptsDev {
     long long trace_cap;
     unsigned long long* trace_count;
     int follow_label;  // records: the attempt takes the label's step (perfect proposal)
-    int method;        // 0: Eq. (3) with the kappa switch; 1: alpha-QSS (FP64 form)
+    int method;        // 0: Eq. (3) with the kappa switch; 1: alpha-QSS (FP64 and mixed forms)
     long long* zone_ns;  // [zones][2]: global timer at queue fetch and at write-back (NULL: off)
     int learn;   // 1: propose with the network
     int record;  // 1: write (features, label) at every accepted state

@@ -32,3 +32,17 @@ def test_roofline_counts_hand_worked():
     # FP64 flops: rates 5 R + fluxes 3 (2-body) + 1 (1-body) + gathers 6 per step, 11 N per attempt
     assert bench.algorithmic_flops(net, 10, 5) == 10 * (10 + 4 + 6) + 15 * 33
     assert bench.update_fp64_flops(net, 15) == 15 * 33
+
+
+def test_qss_roofline_counts_hand_worked():
+    # the same network: a QSS attempt adds the predicted state's rates, fluxes
+    # and gathers (20 FP64 operations, as per accepted step) and 49 N = 147
+    net = custom_network([1.0, 1.0, 2.0], [((0, 1), (2,)), ((2,), (0, 1))], [0.0, 0.0], [0.0, 0.0])
+    assert bench.algorithmic_flops_qss(net, 10, 5) == 10 * 20 + 15 * (20 + 147)
+    # shared memory: the plan's 56 B per accepted step, and again per attempt
+    clk = {"sm_mhz": 1000.0}
+    r = bench.smem_roofline([(net, 10, 5)], 1.0, clk, 1, qss=True)
+    assert r["algorithmic_smem_bytes_per_launch"] == 10 * 56 + 15 * 56
+    # fuller count: the flux and gather part (108 B) again per attempt, the
+    # update (84 B per attempt) once
+    assert r["full_count_smem_bytes_per_launch"] == 10 * 108 + 15 * 84 + 15 * 108
