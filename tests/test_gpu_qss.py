@@ -196,3 +196,41 @@ def test_qss_refuses_other_forms(kn):
         kn.integrate_batch([g], kn.Opts(precision=M64, method=QSS))
     with pytest.raises(kn.KnError, match="opts.method"):
         kn.integrate_batch([g], kn.Opts(precision=FP64, method=7))
+
+
+@pytest.mark.parametrize("prec", [FP64, MIXED])
+def test_qss_operator_split_and_energy(kn, oracle_mod, prec):
+    """The hydro-split driver (Sec. 4 and 6: conditions held per interval, the
+    last dt carried over) with the QSS update: every interval against the
+    oracle's QSS from the oracle's own previous state, and the energy
+    release of each interval."""
+    from kn_inputs import binding_energies
+    from paper_1409_5826_gb300 import opsplit
+    net = net150()
+    B = binding_energies(net)
+    Z = 8
+    z = profile_zones(net, Z, t_end=1e-11)
+    edges = [1e-12, 4e-12, 1e-11, 2e-11]
+    schedule = [(z.T0 * (1 - 0.04 * k), z.rho0 * (1 - 0.08 * k), np.full(Z, edges[k + 1]))
+                for k in range(len(edges) - 1)]
+    g = kn.Network(net)
+    g.set_binding_energies(B)
+    res = opsplit.run(g, z, schedule, kn.Opts(precision=prec, method=QSS))
+    orc = oracle_mod.Oracle(net)
+    opts = oracle_mod.OracleOpts(method=QSS)
+    for i in range(Z):
+        Y = z.Y0[i].copy()
+        dt = z.dt_trial[i]
+        for k, (T9, rho, te) in enumerate(schedule):
+            zk = Zones(Y0=Y[None, :], T0=np.array([T9[i]]), rho0=np.array([rho[i]]), tau=np.zeros(1),
+                       t_start=np.array([edges[k]]), t_end=np.array([te[i]]), dt_trial=np.array([dt]))
+            r = orc.integrate(zk, 0, opts)
+            assert r["status"] == 0
+            got = res[k]
+            assert got["status"][i] == 0 and got["t"][i] == te[i]
+            assert _rel_err(got["Y"][i], r["Y"], 1e-10) < 10 * 0.05
+            y_before = z.Y0[i] if k == 0 else res[k - 1]["Y"][i]
+            assert got["energy"][i] == pytest.approx(float(B @ (got["Y"][i] - y_before)), rel=1e-9, abs=1e-12)
+            e_ref = float(B @ (r["Y"] - Y))
+            assert got["energy"][i] == pytest.approx(e_ref, rel=0.05, abs=1e-3 * abs(e_ref) + 1e-6)
+            Y, dt = r["Y"], r["dt_next"]

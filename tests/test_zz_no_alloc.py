@@ -42,13 +42,13 @@ def _outputs(torch, Z, N):
             "status": torch.empty(Z, dtype=torch.int32, device=dev)}
 
 
-@pytest.mark.parametrize("prec", [1, 0])
-def test_noalloc_matches_batch_on_two_calls(env, prec):
+@pytest.mark.parametrize("prec,method", [(1, 0), (0, 0), (1, 1), (0, 1)])
+def test_noalloc_matches_batch_on_two_calls(env, prec, method):
     torch, kn = env
     net = net150()
     Z = 300
     z = profile_zones(net, Z, t_end=3e-11)
-    opts = kn.Opts(precision=prec, threads_per_zone=160, threads_per_cta=160 if prec == 0 else 800)
+    opts = kn.Opts(precision=prec, method=method, threads_per_zone=160, threads_per_cta=160 if prec == 0 else 800)
     g = kn.Network(net)
     # set-up: the existing entry point builds the network's tables for these opts
     g.set_zones(z)
