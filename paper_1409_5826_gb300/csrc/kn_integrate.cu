@@ -1001,7 +1001,10 @@ __device__ __forceinline__ void gather_pass(const PlanDev& P, const GroupPtrs& g
     }
 }
 
-template <int PREC, bool FEAT, bool QSS>
+// TB_SHARED: the caller passes tb derived from the CTA's shared-memory array
+// (staged tables), so that the compiler addresses the tables as shared memory
+// rather than through generic pointers; the code is the same otherwise.
+template <int PREC, bool FEAT, bool QSS, bool TB_SHARED>
 __device__ void run_group(const PlanDev& P, const OptsDev& O, const unsigned char* tb, const unsigned char* mlp_smem,
                           unsigned char* gbase, const int lane, const GroupSync gs) {
     using real = typename PrecTraits<PREC>::real;
@@ -1477,7 +1480,13 @@ __global__ void __launch_bounds__(1024, 1) integrate_kernel(const __grid_constan
         const int g = threadIdx.x / P.G, lane = threadIdx.x - g * P.G;
         if (g < P.M) {
             GroupSync gs{1 + g, P.G, P.M == 1 && P.G == (int)blockDim.x};
-            run_group<PREC, FEAT, QSS>(P, lp.o, tb, smem, smem + toff + g * P.gl.bytes, lane, gs);
+            unsigned char* gbase = smem + toff + g * P.gl.bytes;
+            // the mixed form with staged tables (the common case) gets its own
+            // copy of the group loop with the tables known to be shared memory
+            if (PREC == kPrecMixed && !FEAT && P.smem_tables)
+                run_group<PREC, FEAT, QSS, true>(P, lp.o, smem + moff, smem, gbase, lane, gs);
+            else
+                run_group<PREC, FEAT, QSS, false>(P, lp.o, tb, smem, gbase, lane, gs);
         }
         __syncthreads();
     }
