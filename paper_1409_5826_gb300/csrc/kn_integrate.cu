@@ -1485,7 +1485,7 @@ __global__ void __launch_bounds__(1024, 1) integrate_kernel(const __grid_constan
             // own copy of the group loop with the tables known to be shared
             // memory (measured: mixed +2.9 %, mixed with the FP64 update +0.7 %;
             // the FP64 form, FP64-pipe bound, within noise)
-            if (PREC != kPrecFP64 && !FEAT && P.smem_tables)
+            if (PREC != kPrecFP64 && P.smem_tables)
                 run_group<PREC, FEAT, QSS, true>(P, lp.o, smem + moff, smem, gbase, lane, gs);
             else
                 run_group<PREC, FEAT, QSS, false>(P, lp.o, tb, smem, gbase, lane, gs);
