@@ -62,3 +62,32 @@ def test_bad_arguments_return_codes(knmod):
     assert L.kn_create_network(C.byref(d), C.byref(h)) == knmod.KN_ERR_INVALID_ARG
     assert L.kn_destroy_network(None) == knmod.KN_OK
     assert L.kn_integrate_batch(None, 0, None, None) == knmod.KN_ERR_INVALID_ARG
+
+
+def test_struct_fields_match_header_offsets(knmod, tmp_path):
+    """Every field of the binding's ctypes mirrors sits at the offset the C
+    compiler gives the same-named member of the header's struct (a host-only
+    C program including include/kn.h prints offsetof and sizeof)."""
+    import shutil
+    import subprocess
+    cc = shutil.which("gcc") or shutil.which("cc")
+    if cc is None:
+        pytest.skip("no C compiler")
+    pairs = [("kn_network_desc", knmod._Desc), ("kn_zone_conditions", knmod._Zones),
+             ("kn_opts", knmod._Opts), ("kn_batch_stats", knmod._Stats), ("kn_tiling", knmod._Tiling)]
+    lines = ["#include <stddef.h>", "#include <stdio.h>", '#include "kn.h"', "int main(void) {"]
+    for cname, py in pairs:
+        lines.append(f'  printf("{cname} sizeof %zu\\n", sizeof({cname}));')
+        for f in py._fields_:
+            lines.append(f'  printf("{cname} {f[0]} %zu\\n", offsetof({cname}, {f[0]}));')
+    lines += ["  return 0;", "}"]
+    src = tmp_path / "offsets.c"
+    src.write_text("\n".join(lines) + "\n")
+    exe = tmp_path / "offsets"
+    subprocess.run([cc, "-std=c99", "-I", os.path.join(ROOT, "include"), str(src), "-o", str(exe)], check=True)
+    out = subprocess.run([str(exe)], check=True, capture_output=True, text=True).stdout.split("\n")
+    got = {tuple(l.split()[:2]): int(l.split()[2]) for l in out if l.strip()}
+    for cname, py in pairs:
+        assert got[(cname, "sizeof")] == C.sizeof(py), cname
+        for f in py._fields_:
+            assert got[(cname, f[0])] == getattr(py, f[0]).offset, (cname, f[0])
