@@ -169,53 +169,62 @@ struct GroupPtrs {
 // alpha(x), x = k dt >= 0, is the rational approximation
 // N/D = (180 r^3 + 60 r^2 + 11 r + 1) / (360 r^3 + 60 r^2 + 12 r + 1), r = 1/x,
 // of 1/(1 - e^-x) - 1/x, the alpha that makes the step exact for constant F+
-// and k.  The corrector's weights a = alpha and b = 1 - alpha = (D - N)/D,
-// with D - N = 180 r^3 + r, so that b keeps its relative accuracy as
-// alpha -> 1.  Horner forms in x up to x = 1 (numerators and denominator
-// times x^3), in r above, so nothing overflows and x = 0 gives 1/2, 1/2.
-__device__ __forceinline__ void qss_weights(double x, double& a, double& b) {
-    double n, d, dn;
-    if (x <= 1.0) {
-        n = fma(fma(x + 11.0, x, 60.0), x, 180.0);
-        d = fma(fma(x + 12.0, x, 60.0), x, 360.0);
-        dn = fma(x, x, 180.0);
-    } else {
-        const double r = 1.0 / x;
-        n = fma(fma(fma(180.0, r, 60.0), r, 11.0), r, 1.0);
-        d = fma(fma(fma(360.0, r, 60.0), r, 12.0), r, 1.0);
-        dn = r * fma(180.0 * r, r, 1.0);
-    }
-    const double inv = 1.0 / d;
-    a = n * inv;
-    b = dn * inv;
+// and k; times x^3, N = x^3 + 11 x^2 + 60 x + 180, D = x^3 + 12 x^2 + 60 x + 360
+// and D - N = x^2 + 180.
+//
+// The scheme's update of one species is y + h (f - k y) / (1 + alpha(k h) k h),
+// with f the production term (F+ in the predictor, the corrector's blend
+// a F+p + (1 - a) F+).  As printed it is a difference of nearly equal terms
+// once k h >> 1 (the result is about 12 y / (k h)^2 + f / k), which rounding
+// would leave with a relative error of about eps (k h)^2 / 12; the same
+// function is evaluated as (c0 y + c1 h f) / c2 from 1 + alpha x = (D + x N)/D
+// and 1 - (1 - alpha) x = (D - x (D - N))/D:
+//   c0 = 12 x^2 - 120 x + 360 (> 0 for every x), c1 = D,
+//   c2 = D + x N = x^4 + 12 x^3 + 72 x^2 + 240 x + 360,
+// so y, f >= 0 give a result >= 0.  In the corrector c1 h f = h (N F+p +
+// (D - N) F+): the blend's denominator cancels and each update costs one
+// division.  Up to x = 2^100 these polynomials in x cannot overflow; above,
+// the same functions are taken in powers of r = 1/x (divided through by x^4).
+constexpr double kQssXMax = 1.2676506002282294e30;  // 2^100
+
+__device__ __forceinline__ void qss_coeffs_x(double x, double& c0, double& c2) {
+    c0 = fma(fma(12.0, x, -120.0), x, 360.0);
+    c2 = fma(fma(fma(x + 12.0, x, 72.0), x, 240.0), x, 360.0);
 }
 
-// The scheme's update of one species, y + h (f - k y) / (1 + alpha(k h) k h),
-// with f the production term (F+ in the predictor, the corrector's blend).
-// As printed it is a difference of nearly equal terms once k h >> 1 (the
-// result is about 12 y / (k h)^2 + f / k), which rounding would leave with a
-// relative error of about eps (k h)^2 / 12; the same function is evaluated as
-// (c0 y + c1 h f) / c2 from 1 + alpha x = (D + x N)/D and
-// 1 - (1 - alpha) x = (D - x (D - N))/D, x = k h:
-//   x <= 1: c0 = 12 x^2 - 120 x + 360, c1 = x^3 + 12 x^2 + 60 x + 360,
-//           c2 = x^4 + 12 x^3 + 72 x^2 + 240 x + 360;
-//   x > 1 (divided through by x^4, r = 1/x): c0 = r^2 (360 r^2 - 120 r + 12),
-//           c1 = r (360 r^3 + 60 r^2 + 12 r + 1), c2 = 360 r^4 + 240 r^3 + 72 r^2 + 12 r + 1.
-// c0 > 0 for every x, so y, f >= 0 give a result >= 0.
+// The predictor's update, production f.
 __device__ __forceinline__ double qss_update1(double y, double f, double k, double h) {
     const double x = k * h;
-    double c0, c1, c2;
-    if (x <= 1.0) {
-        c0 = fma(fma(12.0, x, -120.0), x, 360.0);
-        c1 = fma(fma(x + 12.0, x, 60.0), x, 360.0);
-        c2 = fma(fma(fma(x + 12.0, x, 72.0), x, 240.0), x, 360.0);
-    } else {
-        const double r = 1.0 / x;
-        c0 = fma(fma(360.0, r, -120.0), r, 12.0) * (r * r);
-        c1 = fma(fma(fma(360.0, r, 60.0), r, 12.0), r, 1.0) * r;
-        c2 = fma(fma(fma(fma(360.0, r, 240.0), r, 72.0), r, 12.0), r, 1.0);
+    if (x <= kQssXMax) {
+        double c0, c2;
+        qss_coeffs_x(x, c0, c2);
+        const double c1 = fma(fma(x + 12.0, x, 60.0), x, 360.0);
+        return fma(c0, y, c1 * (h * f)) / c2;
     }
+    const double r = 1.0 / x;
+    const double c0 = fma(fma(360.0, r, -120.0), r, 12.0) * (r * r);
+    const double c1 = fma(fma(fma(360.0, r, 60.0), r, 12.0), r, 1.0) * r;
+    const double c2 = fma(fma(fma(fma(360.0, r, 240.0), r, 72.0), r, 12.0), r, 1.0);
     return fma(c0, y, c1 * (h * f)) / c2;
+}
+
+// The corrector's update: kbar, the predicted state's F+p and the current
+// state's F+ (f0).
+__device__ __forceinline__ double qss_correct1(double y, double fp, double f0, double kbar, double h) {
+    const double x = kbar * h;
+    if (x <= kQssXMax) {
+        double c0, c2;
+        qss_coeffs_x(x, c0, c2);
+        const double n = fma(fma(x + 11.0, x, 60.0), x, 180.0);
+        const double dn = fma(x, x, 180.0);
+        return fma(c0, y, h * fma(n, fp, dn * f0)) / c2;
+    }
+    // weights a = N/D and 1 - a = (D - N)/D in powers of r, then the update
+    const double r = 1.0 / x;
+    const double n = fma(fma(fma(180.0, r, 60.0), r, 11.0), r, 1.0);
+    const double d = fma(fma(fma(360.0, r, 60.0), r, 12.0), r, 1.0);
+    const double dn = r * fma(180.0 * r, r, 1.0);
+    return qss_update1(y, fma(n, fp, dn * f0) / d, kbar, h);
 }
 
 // Predictor: Yp = Y + h (F+ - k Y) / (1 + alpha(k h) k h) from buffer cur into
@@ -301,10 +310,7 @@ __device__ __forceinline__ void update_reduce_fp64(const PlanDev& P, const OptsD
         const double y = Yc[i], fp = Fk[2 * i], kk = Fk[2 * i + 1];
         double yn;
         if (QSS) {
-            const double kbar = 0.5 * (kk + Fk2[2 * i + 1]);
-            double a, b;
-            qss_weights(kbar * h, a, b);
-            yn = qss_update1(y, fma(a, Fk2[2 * i], b * fp), kbar, h);
+            yn = qss_correct1(y, Fk2[2 * i], fp, 0.5 * (kk + Fk2[2 * i + 1]), h);
         } else {
             const double kdt = kk * h;
             yn = (kdt >= kappa) ? (y + h * fp) / (1.0 + kdt) : y + h * (fp - kk * y);
