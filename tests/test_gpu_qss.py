@@ -234,3 +234,47 @@ def test_qss_operator_split_and_energy(kn, oracle_mod, prec):
             e_ref = float(B @ (r["Y"] - Y))
             assert got["energy"][i] == pytest.approx(e_ref, rel=0.05, abs=1e-3 * abs(e_ref) + 1e-6)
             Y, dt = r["Y"], r["dt_next"]
+
+
+@pytest.mark.parametrize("prec", [FP64, MIXED])
+def test_qss_edge_cases(kn, oracle_mod, prec):
+    """Statuses through the QSS path: invalid device inputs, the step limit
+    (with the end state of the oracle's QSS after the same 50 steps), the
+    reject limit, dt underflow, and an interval shorter than the trial dt."""
+    import torch
+    net = net150()
+    g = kn.Network(net)
+    z = constant_zones(net, 3, t_end=1e-11)
+    dz = {k: torch.from_numpy(np.ascontiguousarray(getattr(z, k))).cuda()
+          for k in ("Y0", "T0", "rho0", "tau", "t_start", "t_end", "dt_trial")}
+    dz["Y0"][1, 7] = float("nan")
+    dz["rho0"][2] = -1.0
+    g.set_zones(dz)
+    kn.integrate_batch([g], kn.Opts(precision=prec, method=QSS))
+    assert g.get()["status"].tolist() == [0, 5, 5]
+    z = constant_zones(net, 3, t_end=1e-9)
+    g.set_zones(z)
+    kn.integrate_batch([g], kn.Opts(precision=prec, method=QSS, max_steps=50))
+    r = g.get()
+    assert (r["status"] == 1).all() and (r["steps"] == 50).all()
+    assert (r["t"] < z.t_end).all()
+    ref = oracle_mod.Oracle(net).integrate(z, 0, oracle_mod.OracleOpts(method=QSS, max_steps=50))
+    assert ref["status"] == 1 and ref["steps"] == 50
+    assert _rel_err(r["Y"][0], ref["Y"], 1e-10) < (1e-9 if prec == FP64 else 10 * 0.05)
+    g.set_zones(z)
+    kn.integrate_batch([g], kn.Opts(precision=prec, method=QSS, max_reject=0, grow_max=1e6, safety=1e6))
+    r = g.get()
+    assert (r["status"] == 4).all() and (r["rejects"] >= 1).all()
+    # a reject whose halved step falls below dt_min_frac * t: DT_UNDERFLOW
+    g.set_zones(z)
+    kn.integrate_batch([g], kn.Opts(precision=prec, method=QSS, dt_min_frac=0.9))
+    r = g.get()
+    ref = oracle_mod.Oracle(net).integrate(z, 0, oracle_mod.OracleOpts(method=QSS, dt_min_frac=0.9))
+    assert ref["status"] == 2 and (r["status"] == 2).all()
+    z = constant_zones(net, 1, t_end=1e-12 + 1e-15)
+    g.set_zones(z)
+    kn.integrate_batch([g], kn.Opts(precision=prec, method=QSS))
+    r = g.get()
+    ref = oracle_mod.Oracle(net).integrate(z, 0, oracle_mod.OracleOpts(method=QSS))
+    assert r["status"][0] == 0 and r["t"][0] == z.t_end[0] == ref["t"]
+    assert abs(r["steps"][0] - ref["steps"]) <= max(2, (0.02 if prec == FP64 else 0.05) * ref["steps"])
