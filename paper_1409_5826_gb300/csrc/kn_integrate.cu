@@ -288,6 +288,11 @@ __device__ __forceinline__ void qss_predict_mixed(const PlanDev& P, const GroupP
     }
 }
 
+// Warps of a group that hold species (species i goes to lane i mod G): a warp
+// whose first lane is at or past N has none, skips the update and its
+// reductions, and is left out of the combine.
+__device__ __forceinline__ int species_warps(const PlanDev& P) { return (min(P.G, P.N) + 31) >> 5; }
+
 // (d) the update with step h from buffer cur into nxt, and each warp's share
 // of the error measures (no barrier inside).  FP64 form: every step in FP64,
 // in the order of the definitions.  QSS = false: the kappa-switched update
@@ -298,6 +303,7 @@ __device__ __forceinline__ void qss_predict_mixed(const PlanDev& P, const GroupP
 template <bool QSS>
 __device__ __forceinline__ void update_reduce_fp64(const PlanDev& P, const OptsDev& O, const GroupPtrs& g, int lane,
                                                    int cur, double h, int z) {
+    if ((lane & ~31) >= P.N) return;  // a warp without species
     const int N = P.N, G = P.G, NP1 = N + 1;
     const double* Fk = (const double*)g.Fk;
     const double* Fk2 = (const double*)g.Fk2;
@@ -374,9 +380,10 @@ __device__ __forceinline__ void two_sum(float a, float b, float& s, float& e) {
 template <bool QSS>
 __device__ __forceinline__ void update_reduce_mixed(const PlanDev& P, const OptsDev& O, const GroupPtrs& g, int lane,
                                                     int cur, float h32, int z) {
+    if ((lane & ~31) >= P.N) return;  // a warp without species
     const int N = P.N, G = P.G, NP1 = N + 1;
-    const float2* Fk = (const float2*)g.Fk;
-    const float2* Fk2 = (const float2*)g.Fk2;  // (F+_i, k_i)
+    const float2* Fk = (const float2*)g.Fk;    // (F+_i, k_i)
+    const float2* Fk2 = (const float2*)g.Fk2;  // the same for the QSS predicted state
     const float* A = (const float*)g.A;
     const float* Yh = g.Y32 + cur * NP1;
     const float* Yl = g.Ylo + cur * NP1;
@@ -502,6 +509,7 @@ __device__ __forceinline__ void update_reduce_mixed(const PlanDev& P, const Opts
 // (the step proposal), so no FP64 compare or product runs in them.
 __device__ __forceinline__ void update_reduce_mixed64(const PlanDev& P, const OptsDev& O, const GroupPtrs& g,
                                                       int lane, int cur, double h, int z) {
+    if ((lane & ~31) >= P.N) return;  // a warp without species
     const int N = P.N, G = P.G, NP1 = N + 1;
     const float2* Fk = (const float2*)g.Fk;  // (F+_i, k_i)
     const double* A = (const double*)g.A;
@@ -581,7 +589,7 @@ struct TestOutcome {
 };
 template <int PREC>
 __device__ __forceinline__ TestOutcome combine(const PlanDev& P, const OptsDev& O, const GroupPtrs& g) {
-    const int nw = P.G >> 5;
+    const int nw = species_warps(P);
     TestOutcome v{0.0, 0.0, 1.0, 0.f, 0.f, 1, 0};
     if (PREC == kPrecMixed) {
         float ch = 0.f, cl = 0.f;
