@@ -36,6 +36,13 @@ METRIC = "zone-steps/s and zones/s to t_end, 150sp/1604rx batch; learned-Δt vs 
 T_END = 1e-9
 N_ZONES = 4096
 WORKLOAD = "4096 zones x 150sp/1604rx, T9/rho profiles, t 1e-12 -> 1e-9 s"
+
+
+def workload_name(args):
+    """The workload's name: the default batch's, or one built from --zones and --t-end."""
+    if (args.zones, args.t_end) == (N_ZONES, T_END):
+        return WORKLOAD
+    return f"{args.zones} zones x 150sp/1604rx, T9/rho profiles, t 1e-12 -> {args.t_end:g} s"
 # the uneven-size batch: 2048 zones, 1:2:1, the chain over its own interval
 MIXED_ZONES = 2048
 
@@ -245,7 +252,7 @@ def run_reference(args, rank, world):
             "warmup": args.warmup, "ms_per_step": 1e3 * el / args.steps, "higher_is_better": True,
             "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
             "impl": "reference", "zones_per_s": tot_zones / el,
-            "config": {"workload": WORKLOAD, "zones": args.zones, "sample_zones": len(pick)},
+            "config": {"workload": workload_name(args), "zones": args.zones, "sample_zones": len(pick)},
             "cpu_baseline": {"value": v, "unit": "zone-steps/s", "cores": threads, "kind": "oracle",
                              "sample": f"{len(pick)} of the {args.zones} zones (evenly spaced), each step"},
             "e2e": {"value": v, "unit": "zone-steps/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
@@ -908,8 +915,7 @@ def main():
             "warmup": max(3, args.warmup), "ms_per_step": ms / args.steps, "higher_is_better": True,
             "scaling": "strong" if args.strong else "weak", "vs_baseline": None, "dtype": dtype,
             "data": "synthetic", "zones_per_s": zones_all * args.steps / (ms / 1e3),
-            "config": {"workload": WORKLOAD if (args.zones, args.t_end) == (N_ZONES, T_END) else
-                       f"{args.zones} zones x 150sp/1604rx, T9/rho profiles, t 1e-12 -> {args.t_end:g} s",
+            "config": {"workload": workload_name(args),
                        "zones_per_gpu": zones.n_zones, "n_species": 150, "n_reactions": 1604,
                        "form": args.form, "l2": "flushed between timed steps (256 MB write)",
                        "accepted_steps_per_batch": int(steps_per_batch), "rejects_per_batch": int(st["rejects"]),

@@ -46,3 +46,26 @@ def test_qss_roofline_counts_hand_worked():
     # fuller count: the flux and gather part (108 B) again per attempt, the
     # update (84 B per attempt) once
     assert r["full_count_smem_bytes_per_launch"] == 10 * 108 + 15 * 84 + 15 * 108
+
+
+def test_reference_arm_line_keeps_the_contract():
+    """`bench.py --impl reference` (the oracle on a bounded sample, CPU only)
+    prints one JSON line with the contract's keys, on a short interval."""
+    import json
+    import os
+    import subprocess
+    import sys
+    root = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+    out = subprocess.run([sys.executable, os.path.join(root, "bench.py"), "--impl", "reference", "--steps", "1",
+                          "--warmup", "0", "--t-end", "3e-12"], cwd=root, capture_output=True, text=True,
+                         timeout=600, check=True).stdout.strip().splitlines()
+    assert len(out) == 1
+    d = json.loads(out[0])
+    for k in ("metric", "value", "unit", "n_gpus", "steps", "warmup", "ms_per_step", "higher_is_better", "scaling",
+              "vs_baseline", "dtype", "data", "config", "impl", "cpu_baseline", "e2e"):
+        assert k in d, k
+    assert d["impl"] == "reference" and d["value"] > 0 and d["higher_is_better"] is True
+    assert d["unit"] == "zone-steps/s" and d["config"]["workload"].endswith("3e-12 s")
+    assert d["cpu_baseline"]["kind"] == "oracle" and d["cpu_baseline"]["value"] == d["value"]
+    assert d["cpu_baseline"]["cores"] >= 1 and "sample" in d["cpu_baseline"]
+    assert d["e2e"] == {"value": d["value"], "unit": d["unit"], "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}
