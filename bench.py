@@ -206,6 +206,17 @@ def _profile_line(name):
     return (int(m.group(1)), int(m.group(2)), m.group(3)) if m else None
 
 
+def _profile_issue_line(name):
+    """The issue line of a committed ncu summary:
+    `issue: active_pct=<P> lsu_pct=<Q> sources_sha256=<H>`; (P, Q, hash) or None."""
+    import re
+    path = os.path.join(ROOT, "profiles", name)
+    if not os.path.exists(path):
+        return None
+    m = re.search(r"issue: active_pct=([0-9.]+) lsu_pct=([0-9.]+) sources_sha256=([0-9a-f]+)", open(path).read())
+    return (float(m.group(1)), float(m.group(2)), m.group(3)) if m else None
+
+
 def kernel_sources_sha256():
     """Hash of the code that defines the integrator kernel and its tables,
     with comments and blank lines removed (launch, tiling and autotuner code,
@@ -898,6 +909,14 @@ def main():
     roof["traffic"] = traffic
     roof["traffic_source"] = ("ncu capture of the mixed-form kernel on 1216 zones (committed summary), "
                               "scaled by zones") if traffic else None
+    # the binding resource itself: instruction issue, from the same committed
+    # capture (null when the kernel's sources changed since, or another form)
+    iss = _profile_issue_line("integrate_kernel_mixed_1216x150_full.md")
+    roof["issue"] = None
+    if iss and args.form == "mixed" and iss[2] == kernel_sources_sha256():
+        roof["issue"] = {"active_frac": iss[0] / 100.0, "lsu_pipe_frac": iss[1] / 100.0,
+                         "source": "ncu smsp__issue_active and sm__inst_executed_pipe_lsu of the mixed-form "
+                                   "kernel on 1216 zones (committed summary)"}
     if traffic:
         # context: the DRAM side is far from its bound
         peaks, src = _peaks()

@@ -69,3 +69,13 @@ def test_reference_arm_line_keeps_the_contract():
     assert d["cpu_baseline"]["kind"] == "oracle" and d["cpu_baseline"]["value"] == d["value"]
     assert d["cpu_baseline"]["cores"] >= 1 and "sample" in d["cpu_baseline"]
     assert d["e2e"] == {"value": d["value"], "unit": d["unit"], "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}
+
+
+def test_committed_profile_lines_parse():
+    """The committed summary of the headline kernel carries both machine-readable
+    lines bench.py reads (DRAM bytes per launch; issue and LSU activity)."""
+    t = bench._profile_line("integrate_kernel_mixed_1216x150_full.md")
+    i = bench._profile_issue_line("integrate_kernel_mixed_1216x150_full.md")
+    assert t is not None and t[1] == 1216 and t[0] > 0
+    assert i is not None and 0.0 < i[0] <= 100.0 and 0.0 < i[1] <= 100.0
+    assert len(t[2]) == len(i[2]) == 64
